@@ -1,0 +1,295 @@
+"""FP64 CPU oracle of the sparse-octree tree-code (arXiv:1106.1900).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline legs of ``bench.py`` use this package.  It shares no code with
+the CUDA library (``paper_1106_1900_gb300``) and never imports it.
+
+The arithmetic lives in ``bh_oracle.c`` (plain C, FP64, built with gcc);
+this module compiles it on first use and marshals numpy arrays.  Each
+function names the passage of the paper it follows; the readings taken where
+the paper is silent are listed at the top of ``bh_oracle.c``.
+
+Parity pins (tests marked ``not gpu``) tie it to things other than itself:
+the paper's worked examples (App. A scan, §2.1 mask footnote, App. B dilate),
+brute-force recursive octrees on tiny inputs, numpy's stable sort, closed
+forms (two-body moments, Plummer potential), theta -> 0 reproducing the
+direct sum, and momentum conservation of the direct sum.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bh_oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LEVELS = 20
+
+
+def build(force: bool = False) -> str:
+    """Compile ``bh_oracle.c`` into ``liboracle.so`` (gcc, OpenMP if available)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", _SRC, "-o", _SO + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i64, i32, dbl, u32, p = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint32, ctypes.c_void_p
+            sig = {
+                "or_dilate10": (u32, [u32]),
+                "or_frames": (ctypes.c_int, [i64, p, i32, p, p]),
+                "or_keys": (ctypes.c_int, [i64, p, i32, p, p, p, p, p]),
+                "or_sort": (ctypes.c_int, [i64, p, p, p]),
+                "or_build_levels": (i64, [i64, p, p, i32, i64, p, p, p, p, p]),
+                "or_link": (ctypes.c_int, [i64, p, p, p, p, p, p, p]),
+                "or_groups": (i64, [i64, p, p, p, p, p, p, i32, i64, p, p]),
+                "or_moments": (ctypes.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+                "or_walk": (ctypes.c_int, [i64, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, p, p, i64, p, p,
+                                           dbl, dbl, p, p, p]),
+                "or_direct": (ctypes.c_int, [i64, p, p, i32, p, i64, p, dbl, p, p]),
+                "or_cell_exact": (ctypes.c_int, [i64, i64, p, p, p, dbl, p, p]),
+                "or_cell_multipole": (ctypes.c_int, [dbl, p, p, p, dbl, p, p]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _offsets(n: int, offsets) -> np.ndarray:
+    if offsets is None:
+        return np.array([0, n], dtype=np.int64)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    assert off[0] == 0 and off[-1] == n and np.all(np.diff(off) >= 0)
+    return off
+
+
+# ---------------------------------------------------------------- App. B
+def dilate10(v: int) -> int:
+    """App. B (Listing 1): bit b of the low 10 bits moved to bit 3b."""
+    return int(_load().or_dilate10(v))
+
+
+def frames(pos: np.ndarray, offsets=None) -> np.ndarray:
+    """Per-system frame ``[origin_x, origin_y, origin_z, L]`` (App. B reading)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    off = _offsets(len(pos), offsets)
+    fr = np.zeros((len(off) - 1, 4))
+    _load().or_frames(len(pos), _p(pos), len(off) - 1, _p(off), _p(fr))
+    return fr
+
+
+def keys(pos: np.ndarray, offsets=None, frame=None):
+    """Quantised coordinates ``q[N,3]``, 60-bit Morton keys and system ids."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    off = _offsets(len(pos), offsets)
+    fr = frames(pos, off) if frame is None else np.ascontiguousarray(frame, dtype=np.float64)
+    n = len(pos)
+    q = np.zeros((n, 3), dtype=np.int32)
+    key = np.zeros(n, dtype=np.uint64)
+    sys_ = np.zeros(n, dtype=np.int32)
+    _load().or_keys(n, _p(pos), len(off) - 1, _p(off), _p(fr), _p(q), _p(key), _p(sys_))
+    return q, key, sys_
+
+
+def sort_perm(key: np.ndarray, sys_: np.ndarray) -> np.ndarray:
+    """Stable order by (system, key): ``perm[i]`` = input index of the i-th body (§2.1)."""
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    sys_ = np.ascontiguousarray(sys_, dtype=np.int32)
+    perm = np.zeros(len(key), dtype=np.int64)
+    _load().or_sort(len(key), _p(key), _p(sys_), _p(perm))
+    return perm
+
+
+def cell_bound(n: int, n_leaf: int, n_sys: int = 1) -> int:
+    """Upper bound on the cell count: at most n/(N_leaf+1) nodes per level
+    (levels 0..19) and at most one leaf per body."""
+    return 20 * (n // (n_leaf + 1)) + n + n_sys + 1
+
+
+class Tree:
+    """The oracle's tree: every array is in sorted (system, key) order."""
+
+
+def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None) -> Tree:
+    """§2.1 + §2.2 + §3.2: keys, sort, level-by-level cells, link, groups, moments."""
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    n = len(pos)
+    off = _offsets(n, offsets)
+    nsys = len(off) - 1
+    t = Tree()
+    t.n, t.n_leaf, t.n_crit, t.offsets = n, n_leaf, n_crit, off
+    t.frame = frames(pos, off)
+    t.q, t.key, t.sys = keys(pos, off, t.frame)
+    t.perm = sort_perm(t.key, t.sys)
+    t.skey = np.ascontiguousarray(t.key[t.perm])
+    t.ssys = np.ascontiguousarray(t.sys[t.perm])
+    t.spos = np.ascontiguousarray(pos[t.perm])
+    t.smass = np.ascontiguousarray(mass[t.perm])
+    t.sq = np.ascontiguousarray(t.q[t.perm])
+    cap = cell_bound(n, n_leaf, nsys)
+    level = np.zeros(cap, dtype=np.int32)
+    pbeg = np.zeros(cap, dtype=np.int64)
+    pend = np.zeros(cap, dtype=np.int64)
+    is_leaf = np.zeros(cap, dtype=np.int32)
+    csys = np.zeros(cap, dtype=np.int32)
+    C = lib.or_build_levels(n, _p(t.skey), _p(t.ssys), n_leaf, cap, _p(level), _p(pbeg), _p(pend), _p(is_leaf),
+                            _p(csys))
+    if C < 0:
+        raise RuntimeError("oracle: cell capacity exceeded")
+    t.C = int(C)
+    t.level, t.pbeg, t.pend = level[:C].copy(), pbeg[:C].copy(), pend[:C].copy()
+    t.is_leaf, t.csys = is_leaf[:C].copy(), csys[:C].copy()
+    t.parent = np.zeros(C, dtype=np.int64)
+    t.first_child = np.zeros(C, dtype=np.int64)
+    t.n_children = np.zeros(C, dtype=np.int32)
+    rc = lib.or_link(C, _p(t.level), _p(t.pbeg), _p(t.csys), _p(t.skey), _p(t.parent), _p(t.first_child),
+                     _p(t.n_children))
+    if rc != 0:
+        raise RuntimeError("oracle: link failed")
+    gb = np.zeros(n + 1, dtype=np.int64)
+    ge = np.zeros(n + 1, dtype=np.int64)
+    G = lib.or_groups(C, _p(t.level), _p(t.pbeg), _p(t.pend), _p(t.is_leaf), _p(t.first_child),
+                      _p(t.n_children), n_crit, n + 1, _p(gb), _p(ge))
+    if G < 0:
+        raise RuntimeError("oracle: group capacity exceeded")
+    t.G = int(G)
+    t.gbeg, t.gend = gb[:G].copy(), ge[:G].copy()
+    t.gsys = np.ascontiguousarray(t.ssys[t.gbeg]) if G else np.zeros(0, dtype=np.int32)
+    t.sys_root = np.full(nsys, -1, dtype=np.int64)
+    roots = np.nonzero(t.level == 0)[0]
+    t.sys_root[t.csys[roots]] = roots
+    t.M = np.zeros(C)
+    t.com = np.zeros((C, 3))
+    t.Q = np.zeros((C, 6))
+    t.ctr = np.zeros((C, 3))
+    t.size = np.zeros(C)
+    t.delta = np.zeros(C)
+    lib.or_moments(C, _p(t.level), _p(t.pbeg), _p(t.pend), _p(t.csys), _p(t.spos), _p(t.smass), _p(t.sq),
+                   _p(t.frame), _p(t.M), _p(t.com), _p(t.Q), _p(t.ctr), _p(t.size), _p(t.delta))
+    return t
+
+
+def walk(t: Tree, theta: float, eps: float, groups=None):
+    """§2.2 + §3.3 group walk (FP64).
+
+    Returns ``(acc, pot, stats)`` in SORTED order; ``acc``/``pot`` are only
+    filled for bodies of the walked groups (NaN elsewhere).  ``stats`` is a
+    structured view per walked group: cell-list length ``nc``, particle-list
+    length ``np``, index sums ``csum``/``psum`` and the smallest opening
+    margin ``margin``.
+    """
+    lib = _load()
+    grp = np.arange(t.G, dtype=np.int64) if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
+    acc = np.full((t.n, 3), np.nan)
+    pot = np.full(t.n, np.nan)
+    raw = np.zeros((len(grp), 5), dtype=np.int64)
+    lib.or_walk(len(grp), _p(grp), _p(t.gbeg), _p(t.gend), _p(t.gsys), _p(t.sys_root), t.C, _p(t.is_leaf),
+                _p(t.pbeg), _p(t.pend), _p(t.first_child), _p(t.n_children), _p(t.M), _p(t.com), _p(t.Q),
+                _p(t.size), _p(t.delta), t.n, _p(t.spos), _p(t.smass), float(theta), float(eps), _p(acc),
+                _p(pot), _p(raw))
+    stats = {
+        "nc": raw[:, 0].copy(),
+        "np": raw[:, 1].copy(),
+        "csum": raw[:, 2].view(np.uint64).copy(),
+        "psum": raw[:, 3].view(np.uint64).copy(),
+        "margin": raw[:, 4].copy().view(np.float64),
+    }
+    return acc, pot, stats
+
+
+def tree_forces(pos, mass, theta: float, eps: float, n_leaf: int = 16, n_crit: int = 64, offsets=None):
+    """Build + walk all groups; accelerations and potentials in INPUT order."""
+    t = build_tree(pos, mass, n_leaf, n_crit, offsets)
+    acc_s, pot_s, stats = walk(t, theta, eps)
+    acc = np.empty_like(acc_s)
+    pot = np.empty_like(pot_s)
+    acc[t.perm] = acc_s
+    pot[t.perm] = pot_s
+    return acc, pot, t, stats
+
+
+def direct(pos, mass, eps: float, targets=None, offsets=None):
+    """FP64 direct summation over all other bodies of the same system."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    n = len(pos)
+    off = _offsets(n, offsets)
+    tg = np.arange(n, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    acc = np.zeros((len(tg), 3))
+    pot = np.zeros(len(tg))
+    _load().or_direct(n, _p(pos), _p(mass), len(off) - 1, _p(off), len(tg), _p(tg), float(eps), _p(acc), _p(pot))
+    return acc, pot
+
+
+def cell_exact(t: Tree, c: int, x, eps: float = 0.0):
+    """Exact force of cell ``c``'s own bodies on point ``x``."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    a = np.zeros(3)
+    p = np.zeros(1)
+    _load().or_cell_exact(int(t.pbeg[c]), int(t.pend[c]), _p(t.spos), _p(t.smass), _p(x), float(eps), _p(a), _p(p))
+    return a, float(p[0])
+
+
+def cell_multipole(t: Tree, c: int, x, eps: float = 0.0):
+    """Monopole + quadrupole approximation of cell ``c`` at point ``x``."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    a = np.zeros(3)
+    p = np.zeros(1)
+    com = np.ascontiguousarray(t.com[c])
+    Q = np.ascontiguousarray(t.Q[c])
+    _load().or_cell_multipole(float(t.M[c]), _p(com), _p(Q), _p(x), float(eps), _p(a), _p(p))
+    return a, float(p[0])
+
+
+# ------------------------------------------------------------ §3.1, Eq. 3
+def leapfrog_step(x, v, a_old, dt: float, accel):
+    """Leapfrog predictor-corrector (§3.1, after Hut et al. 1995), FP64.
+
+    Predict ``x += v dt + a dt^2/2`` and ``v_p = v + a dt`` with the old
+    acceleration, evaluate ``a_new = accel(x)``, then correct
+    ``v = v_p + (a_new - a_old) dt/2``.  Returns ``(x, v, a_new, pot)``.
+    """
+    x = x + v * dt + 0.5 * a_old * dt * dt
+    vp = v + a_old * dt
+    a_new, pot = accel(x)
+    v = vp + 0.5 * (a_new - a_old) * dt
+    return x, v, a_new, pot
+
+
+def energy(vel, mass, pot):
+    """Kinetic, potential (1/2 sum m phi) and total energy; Eq. 3 uses the total."""
+    ek = 0.5 * float(np.sum(mass * np.sum(vel * vel, axis=1)))
+    ep = 0.5 * float(np.sum(mass * pot))
+    return ek, ep, ek + ep
+
+
+def momentum(vel, mass):
+    return np.sum(mass[:, None] * vel, axis=0)
