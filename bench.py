@@ -1,0 +1,371 @@
+"""Benchmark: particles/s per force step of the tree-code on a 1M-body Plummer sphere.
+
+One "step" is the whole hot path on one batch: FP64 leapfrog predict,
+frame + Morton keys, radix sort, move, cells + links + groups, moments, the
+group walk (theta = 0.5, eps = 0.005) and the FP64 correct, replayed as one
+CUDA graph per step.  Inputs are resident in HBM when the timed region
+starts; L2 is flushed (a 512 MB write) between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own 1M-body system (weak scaling, no
+collective on the data path); the value is the bodies of all ranks divided
+by the slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s per force step (1M Plummer, θ=0.5), batched vs plain, same error"
+UNIT = "particles/s"
+N_BODIES = 1 << 20
+THETA, EPS, DT = 0.5, 0.005, 1.0 / 64
+SEED = 2
+# flops per interaction: FMA = 2, rsqrt = 1, add/sub/mul = 1 (counted from k_walk.cu)
+FLOPS_PP = 20
+FLOPS_PC = 54
+SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_BODIES)
+    ap.add_argument("--theta", type=float, default=THETA)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="launch kernel by kernel instead of the graph")
+    ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def walk_traffic():
+    """Per-launch DRAM bytes of the walk kernel from the committed ncu summary,
+    if it was taken from the current source of the kernel."""
+    src = open(os.path.join(ROOT, "paper_1106_1900_gb300", "csrc", "k_walk.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "walk_plummer_1m.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if m_sha and m_b and m_sha.group(1) == sha:
+        return float(m_b.group(1))
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    the whole tree build plus the walk of every k-th group."""
+    import numpy as np
+
+    import oracle
+
+    t0 = time.perf_counter()
+    t = oracle.build_tree(pos, mass)
+    t_build = time.perf_counter() - t0
+    # size the sample from a short probe so that the walk takes ~target_s
+    probe = np.arange(0, t.G, max(1, t.G // 64))
+    t0 = time.perf_counter()
+    oracle.walk(t, theta, eps, probe)
+    t_probe = time.perf_counter() - t0
+    per_group = t_probe / len(probe)
+    k = max(1, int(t.G * per_group / max(target_s - t_build, 1.0)))
+    groups = np.arange(0, t.G, k)
+    t0 = time.perf_counter()
+    oracle.walk(t, theta, eps, groups)
+    t_walk = time.perf_counter() - t0
+    bodies = int(sum(t.gend[g] - t.gbeg[g] for g in groups))
+    secs = t_walk + t_build * bodies / t.n
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": bodies / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 tree build of all {t.n} bodies ({t_build:.2f} s, charged pro rata) + walk of "
+                      f"every {k}-th group ({len(groups)} groups, {bodies} bodies, {t_walk:.2f} s), "
+                      f"theta={theta}, eps={eps}"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step builds the full tree and walks a sample of groups."""
+    import numpy as np
+
+    import ics
+    import oracle
+
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    pos, vel, m = ics.plummer(args.n, SEED)
+    t0 = time.perf_counter()
+    t = oracle.build_tree(pos, m)
+    t_build = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
+    probe = np.arange(0, t.G, max(1, t.G // 32))
+    t0 = time.perf_counter()
+    oracle.walk(t, args.theta, EPS, probe)
+    per_group = (time.perf_counter() - t0) / len(probe)
+    k = max(1, int(t.G * per_group / max(budget - t_build, 0.5)))
+    groups = np.arange(0, t.G, k)
+    bodies = int(sum(t.gend[g] - t.gbeg[g] for g in groups))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        tt = oracle.build_tree(pos, m)
+        tb = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.walk(tt, args.theta, EPS, groups)
+        tw = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(tw + tb * bodies / tt.n)
+    secs = sum(times)
+    value = bodies * len(times) / secs
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"per step: FP64 tree build of all {args.n} bodies (charged pro rata) + walk of every {k}-th "
+              f"group ({len(groups)} groups, {bodies} bodies)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times) * args.n / bodies,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"Plummer N={args.n}, theta={args.theta}, eps={EPS}, seed={SEED}",
+                   "global_batch": args.n, "parallelism": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import ics
+    import paper_1106_1900_gb300 as bh
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bh.load()
+    n = args.n
+    pos, vel, m = ics.plummer(n, SEED + rank)
+    tc = bh.TreeCode(n, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        P = torch.from_numpy(pos).to(dev)
+        V = torch.from_numpy(vel).to(dev)
+        M = torch.from_numpy(m).to(dev)
+        tc.set_state(P, V, M)
+        tc.set_profiling(True)
+        for _ in range(args.warmup):
+            tc.step(DT, args.theta, EPS, graph=not args.eager)
+        tc.check()
+        torch.cuda.synchronize()
+        tc.reset_counters()
+        c0 = tc.counts()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        step_ms, walk_ms, phases = [], [], []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                if args.flush_mb > 0:
+                    flush.fill_(k & 0xff)
+                ev[k][0].record(stream)
+                tc.step(DT, args.theta, EPS, graph=not args.eager)
+                ev[k][1].record(stream)
+                ph = tc.phase_times()  # synchronises on this step's walk events
+                walk_ms.append(ph["walk"])
+                phases.append(ph)
+            torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        if world > 1:
+            torch.distributed.barrier()
+        tc.check()
+        c1 = tc.counts()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    t_max = max_over_ranks(total_ms, world, dev)
+    bodies_all = sum_over_ranks(float(n * args.steps), world, dev)
+    value = bodies_all / (t_max * 1e-3)
+    launches = c1["launches"] - c0["launches"]
+    # ---- roofline of the dominant kernel (the walk): algorithmic flops / its device time
+    pp, pc = c1["pp"] - c0["pp"], c1["pc"] - c0["pc"]
+    flops = FLOPS_PP * pp + FLOPS_PC * pc
+    walk_s = sum(walk_ms) * 1e-3
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    achieved = flops / walk_s if walk_s > 0 else 0.0
+    traffic = walk_traffic()
+    clocks = clk.summary()
+    mean_phase = {k: statistics.mean(p[k] for p in phases) for k in bh.PHASES if k != "call"}
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(pos).pin_memory()
+        hm = torch.from_numpy(m).pin_memory()
+        ha = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+        hq = torch.empty(n, dtype=torch.float32).pin_memory()
+        tc2 = bh.TreeCode(n, device=local)
+        for _ in range(max(1, args.warmup)):
+            tc2.forces_host(hp, hm, args.theta, EPS, ha, hq, stream=stream)
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = time.perf_counter()
+        for _ in range(args.steps):
+            tc2.forces_host(hp, hm, args.theta, EPS, ha, hq, stream=stream)
+        e_s = max_over_ranks(time.perf_counter() - e0, world, dev)
+        e2e = {"value": bodies_all / e_s, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 8),
+               "d2h_bytes_per_step": n * (12 + 4)}
+        tc2.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pos, m, args.theta, EPS)
+    if rank != 0:
+        return
+    cnt = tc.counts()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Plummer N={n} per GPU (virial units, seed {SEED}+rank), theta={args.theta}, "
+                               f"eps={EPS}, dt=1/64, full leapfrog step as one CUDA graph",
+                   "global_batch": n * world, "parallelism": f"independent system per GPU x{world}",
+                   "l2": f"flushed between timed steps ({args.flush_mb} MB write)" if args.flush_mb else "not flushed",
+                   "n_leaf": tc.params.n_leaf, "n_crit": tc.params.n_crit,
+                   "cells": cnt["cells"], "groups": cnt["groups"], "graph": not args.eager},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": traffic,
+                     "kernel": "k_walk (group walk + interactions)",
+                     "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{SM_MAX_MHZ:.0f} MHz (unit counts and max clock)",
+                     "flops_per_step": flops / args.steps, "pp_per_step": pp / args.steps,
+                     "pc_per_step": pc / args.steps, "walk_ms_mean": statistics.mean(walk_ms)},
+        "phase_ms_mean": mean_phase,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "wall_s_timed": wall1 - wall0,
+    }
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * bh.h -- C ABI of the GB300 (sm_103a) sparse-octree gravitational tree-code.
+ *
+ * The library computes, on one GPU, the per-step force evaluation of the
+ * Barnes-Hut tree-code of Bedorf, Gaburov & Portegies Zwart (arXiv:1106.1900):
+ * Morton keys, radix sort, level-by-level sparse octree, monopole +
+ * quadrupole moments, and the breadth-first group walk with the opening test
+ * d > l/theta + delta (Eq. 1), followed by an FP64 leapfrog step (§3.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Units: G = 1 (N-body units).
+ * - Layout: positions and velocities are [n][3] FP64, row-major; masses [n]
+ *   FP64; accelerations [n][3] FP32; potentials [n] FP32.  Outputs are in the
+ *   caller's input order.  n < 2^31.
+ * - Memory: pointers named *_dev are CUDA device pointers, *_host are host
+ *   pointers.  The caller owns every input and output buffer and the
+ *   workspace.  After bh_bind_workspace the library never allocates device
+ *   memory and never frees caller memory.
+ * - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   Calls are stream-ordered and asynchronous unless stated otherwise;
+ *   input buffers must stay valid until the stream reaches the call.
+ * - Errors: every call returns a bh_status_t code.  Nothing throws across the ABI.
+ *   Errors detected on the device (non-finite input, a full walk stack, a
+ *   bounded wait that gave up) are latched in a device status word that
+ *   bh_status() returns after synchronising the stream.
+ * - Threads: one context must not be used by two host threads at once.
+ */
+#ifndef BH_H
+#define BH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum bh_status_code {
+    BH_OK = 0,
+    BH_ERR_INVALID_ARG = 1, /* bad pointer, size, parameter or offsets */
+    BH_ERR_CAPACITY = 2,    /* n or n_sys above the context's maxima, or a walk
+                               stack overflowed (raise stack_capacity) */
+    BH_ERR_NONFINITE = 3,   /* a position or mass is NaN or infinite */
+    BH_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    BH_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    BH_ERR_STATE = 6,       /* call order violated (e.g. forces before build) */
+    BH_ERR_NO_WORKSPACE = 7 /* no (or too small a) workspace is bound */
+} bh_status_t;
+
+/* Tunables (§2.1, §2.2).  Fill with bh_default_params, then override. */
+typedef struct bh_params {
+    int32_t n_leaf;         /* N_leaf: a cell with <= n_leaf bodies is a leaf (§2.1).
+                               1..64, default 16. */
+    int32_t n_crit;         /* N_crit: a group holds <= n_crit bodies (§2.2).
+                               n_leaf..64, default 64. */
+    int32_t stack_capacity; /* entries per breadth-first level stack of one walking
+                               warp (§2.2 current/next-level stacks), default 16384 */
+    int32_t walk_variant;   /* 0: FP32 in group-relative coordinates with compensated
+                               accumulation across list tiles (default);
+                               1: naive FP32 (absolute coordinates, plain sums) */
+    int32_t walk_warps;     /* warps per walk block, 1..16, default 4 */
+    int32_t walk_blocks_per_sm; /* persistent walk grid = SMs x this; 0 = occupancy */
+    int32_t reserved[2];    /* must be 0 */
+} bh_params;
+
+typedef struct bh_ctx bh_ctx; /* opaque, library-owned host object */
+
+/* Number of per-phase timers reported by bh_phase_times. */
+#define BH_NPHASES 8
+/* Phases: 0 frame+keys, 1 sort, 2 move, 3 cells+link+groups, 4 moments,
+ *         5 walk, 6 leapfrog (predict+correct), 7 whole call. */
+
+/* Writes the defaults into *p.  Returns BH_OK or BH_ERR_INVALID_ARG (p NULL). */
+int bh_default_params(bh_params *p);
+
+/* Device workspace a context created with (p, n_max, n_sys_max) needs, in
+ * bytes, written to *bytes.  The size grows linearly with n_max (cell table
+ * bound 20*floor(n/(n_leaf+1)) + n + n_sys) plus the walk stacks
+ * (SMs x resident warps x 2 x stack_capacity x 4 B) on `device`. */
+int bh_workspace_bytes(const bh_params *p, int64_t n_max, int32_t n_sys_max, int device, size_t *bytes);
+
+/* Creates a context for up to n_max bodies in up to n_sys_max systems on
+ * `device` (made current for the call).  The context holds host state and
+ * CUDA events only; device memory comes from bh_bind_workspace. */
+int bh_create(bh_ctx **out, const bh_params *p, int64_t n_max, int32_t n_sys_max, int device);
+
+/* Binds a caller-allocated device buffer of `bytes` >= bh_workspace_bytes(...)
+ * (256-byte aligned).  The context keeps the pointer; the caller keeps
+ * ownership and must keep it alive until bh_destroy. */
+int bh_bind_workspace(bh_ctx *ctx, void *ws_dev, size_t bytes);
+
+/* Destroys the context (host state, events and captured graphs). */
+void bh_destroy(bh_ctx *ctx);
+
+/* Builds the octree of one system (§2.1, App. B): frame and Morton keys,
+ * stable radix sort, level-by-level cells, links, groups (§2.2) and the
+ * monopole + quadrupole moments (§3.2).  pos_dev [n][3], mass_dev [n]. */
+int bh_build(bh_ctx *ctx, const double *pos_dev, const double *mass_dev, int64_t n, void *stream);
+
+/* The same for a forest of independent systems: system s owns bodies
+ * sys_offsets_host[s] .. sys_offsets_host[s+1]-1 (ascending, [0] = 0,
+ * [n_sys] = n; empty systems allowed).  Each system gets its own frame;
+ * cells and groups never span two systems. */
+int bh_build_forest(bh_ctx *ctx, const double *pos_dev, const double *mass_dev, int64_t n,
+                    const int64_t *sys_offsets_host, int32_t n_sys, void *stream);
+
+/* Accelerations and potentials of every body of the last build (§2.2, §3.3):
+ * groups walk the tree breadth-first, accept cells with d^2 > (l/theta + delta)^2,
+ * and sum softened particle-cell (monopole + quadrupole) and particle-particle
+ * interactions in FP32.  theta > 0 (theta = 0 opens every cell), eps >= 0.
+ * acc_dev [n][3], pot_dev [n], caller order. */
+int bh_compute_forces(bh_ctx *ctx, float theta, float eps, float *acc_dev, float *pot_dev, void *stream);
+
+/* The same round trip from host memory: copies pos/mass in, builds, walks,
+ * copies acc/pot out, and synchronises the stream.  Host buffers should be
+ * pinned for speed. */
+int bh_forces_host(bh_ctx *ctx, const double *pos_host, const double *mass_host, int64_t n,
+                   float theta, float eps, float *acc_host, float *pot_host, void *stream);
+
+/* Loads the integrator state (FP64): n bodies, optional forest offsets
+ * (sys_offsets_host NULL or n_sys <= 1 means one system).  The first bh_step
+ * afterwards first evaluates the accelerations at the loaded positions. */
+int bh_set_state(bh_ctx *ctx, const double *pos_dev, const double *vel_dev, const double *mass_dev, int64_t n,
+                 const int64_t *sys_offsets_host, int32_t n_sys, void *stream);
+
+/* Copies the state out in the order it was loaded; any pointer may be NULL.
+ * acc/pot are the last evaluated accelerations and potentials. */
+int bh_get_state(bh_ctx *ctx, double *pos_dev, double *vel_dev, float *acc_dev, float *pot_dev, void *stream);
+
+/* One leapfrog predictor-corrector step (§3.1): x += v dt + a dt^2/2,
+ * v_p = v + a dt, rebuild the tree at x, evaluate a_new, v = v_p +
+ * (a_new - a) dt/2.  FP64 state, FP32 forces.  No host synchronisation. */
+int bh_step(bh_ctx *ctx, double dt, float theta, float eps, void *stream);
+
+/* bh_step through a CUDA graph: the first call with a given (dt, theta, eps)
+ * captures one step on a context-owned stream and instantiates it; every
+ * call then launches the graph on `stream`. */
+int bh_step_graph(bh_ctx *ctx, double dt, float theta, float eps, void *stream);
+
+/* Energies and momentum of the current state (FP64, synchronises):
+ * out[0] kinetic, out[1] potential = 1/2 sum m phi, out[2..4] momentum.
+ * The potentials are those of the last force evaluation. */
+int bh_diagnostics(bh_ctx *ctx, double out[5], void *stream);
+
+/* Synchronises `stream` and returns (and clears) the device status word. */
+int bh_status(bh_ctx *ctx, void *stream);
+
+/* Sizes of the last build (synchronises): out[0] n, out[1] cells, out[2]
+ * groups, out[3] systems, out[4] deepest level, out[5] walk launches since
+ * reset, out[6] particle-particle and out[7] particle-cell interactions summed
+ * over those launches (self pairs excluded), out[8] kernel launches issued
+ * by the library since reset. */
+int bh_get_counts(bh_ctx *ctx, int64_t out[9], void *stream);
+
+/* Clears the interaction and launch counters of bh_get_counts. */
+int bh_reset_counters(bh_ctx *ctx, void *stream);
+
+/* Exports the integer tree of the last build to host arrays (synchronises);
+ * any pointer may be NULL.  Sorted order: skey[n] 60-bit Morton keys (a
+ * forest orders by system, then key), perm[n] input index of each sorted
+ * body.  Cells (count from bh_get_counts) in (level, system, key) order:
+ * level, pbeg, pend (sorted body range), parent (-1 at a root), first_child
+ * (-1 at a leaf), n_children (0 at a leaf), is_leaf.  Groups in body order:
+ * gbeg, gend. */
+int bh_get_tree(bh_ctx *ctx, uint64_t *skey, int32_t *perm, int32_t *level, int32_t *pbeg, int32_t *pend,
+                int32_t *parent, int32_t *first_child, int32_t *n_children, int32_t *is_leaf, int32_t *gbeg,
+                int32_t *gend, void *stream);
+
+/* Exports the moments of every cell (synchronises), any pointer may be NULL:
+ * mass[C], com[C][3] (FP64, recombined from its two-float form), quad[C][6]
+ * (xx, yy, zz, xy, xz, yz, about the centre of mass), delta[C] =
+ * |com - geometric centre|, size[C] = l. */
+int bh_get_moments(bh_ctx *ctx, float *mass, double *com, float *quad, float *delta, float *size, void *stream);
+
+/* Per-group statistics of the last walk (synchronises): cell-list length,
+ * particle-list length, and the sums of the listed cell and body indices. */
+int bh_get_group_stats(bh_ctx *ctx, int32_t *n_pc, int32_t *n_pp, uint64_t *csum, uint64_t *psum, void *stream);
+
+/* Per-phase device times in milliseconds of the last bh_build +
+ * bh_compute_forces or bh_step (see BH_NPHASES), recorded with CUDA events
+ * when profiling is on (synchronises). */
+int bh_set_profiling(bh_ctx *ctx, int on);
+int bh_phase_times(bh_ctx *ctx, float ms[BH_NPHASES]);
+
+/* Device time in milliseconds of the last walk phase alone (the opening-radius
+ * pass and the walk kernel, phase 5), synchronising on it.  Profiling must be
+ * on. */
+int bh_walk_time(bh_ctx *ctx, float *ms);
+
+/* App. A scan primitive (device-wide exclusive prefix sum of uint32), exposed
+ * for verification: out_dev[i] = in_dev[0] + ... + in_dev[i-1], and
+ * *total_host = the sum of all n values (synchronises).  Needs a bound
+ * workspace and n <= n_max. */
+int bh_prim_exclusive_scan(bh_ctx *ctx, const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_host,
+                           void *stream);
+
+/* A FP32 fused-multiply-add throughput probe: runs `iters` dependent FMA
+ * chains on every resident thread and returns the achieved FP32 FLOP/s
+ * (2 per FMA) in *flops.  Used to state the walk's FP32 roofline. */
+int bh_fp32_peak_probe(int device, int iters, double *flops, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *bh_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BH_H */

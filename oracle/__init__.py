@@ -63,7 +63,7 @@ def _load():
                 "or_groups": (i64, [i64, p, p, p, p, p, p, i32, i64, p, p]),
                 "or_moments": (ctypes.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p, p, p]),
                 "or_walk": (ctypes.c_int, [i64, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, p, p, i64, p, p,
-                                           dbl, dbl, p, p, p]),
+                                           dbl, dbl, p, p, p, p]),
                 "or_direct": (ctypes.c_int, [i64, p, p, i32, p, i64, p, dbl, p, p]),
                 "or_cell_exact": (ctypes.c_int, [i64, i64, p, p, p, dbl, p, p]),
                 "or_cell_multipole": (ctypes.c_int, [dbl, p, p, p, dbl, p, p]),
@@ -204,23 +204,26 @@ def walk(t: Tree, theta: float, eps: float, groups=None):
     filled for bodies of the walked groups (NaN elsewhere).  ``stats`` is a
     structured view per walked group: cell-list length ``nc``, particle-list
     length ``np``, index sums ``csum``/``psum`` and the smallest opening
-    margin ``margin``.
+    margin ``margin``; ``stats["amag"]`` holds, per body (sorted order), the
+    sum of the magnitudes of its interaction terms.
     """
     lib = _load()
     grp = np.arange(t.G, dtype=np.int64) if groups is None else np.ascontiguousarray(groups, dtype=np.int64)
     acc = np.full((t.n, 3), np.nan)
     pot = np.full(t.n, np.nan)
     raw = np.zeros((len(grp), 5), dtype=np.int64)
+    amag = np.full(t.n, np.nan)
     lib.or_walk(len(grp), _p(grp), _p(t.gbeg), _p(t.gend), _p(t.gsys), _p(t.sys_root), t.C, _p(t.is_leaf),
                 _p(t.pbeg), _p(t.pend), _p(t.first_child), _p(t.n_children), _p(t.M), _p(t.com), _p(t.Q),
                 _p(t.size), _p(t.delta), t.n, _p(t.spos), _p(t.smass), float(theta), float(eps), _p(acc),
-                _p(pot), _p(raw))
+                _p(pot), _p(raw), _p(amag))
     stats = {
         "nc": raw[:, 0].copy(),
         "np": raw[:, 1].copy(),
         "csum": raw[:, 2].view(np.uint64).copy(),
         "psum": raw[:, 3].view(np.uint64).copy(),
         "margin": raw[:, 4].copy().view(np.float64),
+        "amag": amag,
     }
     return acc, pot, stats
 
@@ -233,6 +236,9 @@ def tree_forces(pos, mass, theta: float, eps: float, n_leaf: int = 16, n_crit: i
     pot = np.empty_like(pot_s)
     acc[t.perm] = acc_s
     pot[t.perm] = pot_s
+    amag = np.empty_like(pot_s)
+    amag[t.perm] = stats["amag"]
+    stats["amag_input_order"] = amag
     return acc, pot, t, stats
 
 

@@ -331,6 +331,8 @@ int or_moments(int64_t C, const int32_t *level, const int64_t *pbeg, const int64
 
 /* ---------------------------------------------------------- forces (§3) */
 
+static double norm3(const double *v) { return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
 /* Softened particle-cell interaction (monopole + quadrupole), target at x. */
 static void pc_force(const double *x, double M, const double *cm, const double *Q, double eps2, double *acc,
                      double *pot)
@@ -368,12 +370,16 @@ static void pp_force(const double *x, const double *xs, double m, double eps2, d
  *   stats[5*j]:  cell-list length, particle-list length, sum of listed cell
  *                indices, sum of listed body indices, and (as a double bit
  *                pattern) the smallest relative margin |d - r_open|/r_open
- *                of any opening decision of group groups[j]. */
+ *                of any opening decision of group groups[j].
+ *   amag[i]:     sum over the body's interactions of |a_ij| (how much the
+ *                terms of the sum cancel: |a_i| / amag[i] near 0 means the
+ *                result is small against its terms). */
 int or_walk(int64_t ng, const int64_t *groups, const int64_t *gbeg, const int64_t *gend, const int32_t *gsys,
             const int64_t *sys_root, int64_t C, const int32_t *is_leaf, const int64_t *pbeg, const int64_t *pend,
             const int64_t *first_child, const int32_t *n_children, const double *M, const double *com,
             const double *Q, const double *size, const double *delta, int64_t n, const double *spos,
-            const double *smass, double theta, double eps, double *acc, double *pot, int64_t *stats)
+            const double *smass, double theta, double eps, double *acc, double *pot, int64_t *stats,
+            double *amag)
 {
     double eps2 = eps * eps;
 #pragma omp parallel
@@ -429,19 +435,28 @@ int or_walk(int64_t ng, const int64_t *groups, const int64_t *gbeg, const int64_
                 ncur = nnext;
             }
             for (int64_t i = gbeg[g]; i < gend[g]; ++i) {
-                double a[3] = {0, 0, 0}, p = 0.0;
+                double a[3] = {0, 0, 0}, p = 0.0, mag = 0.0;
                 const double *x = spos + 3 * i;
                 for (int64_t t = 0; t < nc; ++t) {
                     int64_t c = clist[t];
-                    pc_force(x, M[c], com + 3 * c, Q + 6 * c, eps2, a, &p);
+                    double ai[3] = {0, 0, 0}, pi = 0.0;
+                    pc_force(x, M[c], com + 3 * c, Q + 6 * c, eps2, ai, &pi);
+                    for (int b = 0; b < 3; ++b) a[b] += ai[b];
+                    p += pi;
+                    mag += norm3(ai);
                 }
                 for (int64_t t = 0; t < np; ++t) {
                     int64_t s = plist[t];
                     if (s == i) continue;
-                    pp_force(x, spos + 3 * s, smass[s], eps2, a, &p);
+                    double ai[3] = {0, 0, 0}, pi = 0.0;
+                    pp_force(x, spos + 3 * s, smass[s], eps2, ai, &pi);
+                    for (int b = 0; b < 3; ++b) a[b] += ai[b];
+                    p += pi;
+                    mag += norm3(ai);
                 }
                 for (int b = 0; b < 3; ++b) acc[3 * i + b] = a[b];
                 pot[i] = p;
+                amag[i] = mag;
             }
             stats[5 * j + 0] = nc;
             stats[5 * j + 1] = np;

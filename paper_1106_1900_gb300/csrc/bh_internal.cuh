@@ -1,0 +1,195 @@
+// bh_internal.cuh -- context layout, launch entry points and device helpers
+// shared by the library's translation units (never by the oracle).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bh.h"
+
+namespace bh {
+
+constexpr int kLevels = 20;         // 60-bit keys, 20 levels below the root (App. B)
+constexpr int kRows = kLevels + 2;  // 21 cell levels + one row of group starts
+constexpr uint32_t kQMax = 1u << 20;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Frame of one system: origin (per-axis minimum) and power-of-two side L.
+struct __align__(32) Frame {
+  double x, y, z, w;
+};
+
+// ------------------------------------------------------------ context
+struct Ctx {
+  bh_params p;
+  int device = 0;
+  int num_sms = 0;
+  int64_t n_max = 0;
+  int32_t s_max = 1;
+  int64_t c_max = 0;   // cell-table bound
+  int walk_grid = 0;   // persistent walk blocks
+  int walk_warps_total = 0;
+  int walk_smem = 0;
+  size_t ws_bytes = 0;
+  char *ws = nullptr;
+
+  // sizes of the current tree
+  int64_t n = 0;
+  int32_t n_sys = 1;
+  bool built = false;       // bh_build* done
+  bool forces = false;      // bh_compute_forces done since build
+  bool have_state = false;  // bh_set_state done
+  bool have_acc = false;    // a_old valid for the state
+  int state_cur = 0;        // which state buffer (0/1) is current
+  int64_t host_offsets_sig = -1;
+
+  // ---- device buffers (carved from the workspace)
+  // per system
+  int32_t *offs;                 // [S+1]
+  unsigned long long *minmax;    // [S][6] order-preserving bits of min xyz, max xyz
+  Frame *frame;                  // [S] origin xyz, L
+  int32_t *sys_root;             // [S]
+  uint32_t *frame_ticket;        // [1]
+  // per body
+  uint64_t *key[2];
+  uint32_t *idx[2];
+  float4 *part_hi, *part_lo;     // sorted bodies: (x_hi, y_hi, z_hi, m), (x_lo, y_lo, z_lo, 0)
+  uint8_t *lohi;                 // [n][2] first level started, last level (leaf level)
+  uint8_t *gstart;               // [n] group start flag
+  float4 *acc_sorted;            // walk output in sorted order (ax, ay, az, phi)
+  double *st_x[2], *st_v[2], *st_m[2];
+  float4 *st_a[2];
+  int32_t *st_id[2];
+  double *h_pos, *h_mass;        // staging for bh_forces_host
+  float *h_acc, *h_pot;
+  // per warp of the level pass
+  uint32_t *rowcnt;              // [kRows][W]
+  uint32_t *rowoff;              // [kRows][W]
+  // per cell
+  int32_t *c_level, *c_pbeg, *c_pend, *c_parent, *c_first, *c_nch;
+  uint32_t *c_ctr;               // bottom-up arrival counters
+  int2 *c_link;                  // walk link {first, count | leaf << 31}
+  float4 *c_mom;                 // [C][4] moments (see k_moments.cu)
+  float4 *c_mac;                 // [C] com_hi xyz, l/theta + delta
+  // per group
+  int32_t *g_beg;                // [G+1]
+  int32_t *g_sys;                // [G]
+  int32_t *g_npc, *g_npp;        // [G] list lengths of the last walk
+  unsigned long long *g_csum, *g_psum;
+  // sort scratch
+  uint32_t *sort_hist;           // [passes][256]
+  uint32_t *sort_status;         // [passes][tiles][256]
+  uint32_t *sort_tile_ctr;       // [passes]
+  int sort_max_passes = 0;
+  int64_t sort_tiles_max = 0;
+  // scan scratch
+  uint32_t *scan_blocks;         // [blocks]
+  uint64_t *scan_total;          // [1]
+  // walk
+  int32_t *walk_stack;           // [warps][2][cap]
+  uint32_t *walk_queue;          // [1]
+  // scalars
+  int32_t *d_counts;             // [0] C, [1] G, [2] max level
+  unsigned long long *d_totals;  // [0] pp, [1] pc, [2] walk launches
+  int32_t *d_status;             // [1]
+  double *d_diag;                // [5 + blocks*5]
+
+  // host side bookkeeping
+  long long launches = 0;
+  bool profiling = false;
+  bool capturing = false;
+  cudaEvent_t ev[BH_NPHASES + 1][2] = {};
+  float phase_ms[BH_NPHASES] = {};
+  bool phase_rec[BH_NPHASES] = {};
+  cudaStream_t cap_stream = nullptr;
+  // one captured step per state-buffer parity (the state swaps buffers every step)
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  long long graph_launches[2] = {0, 0};
+  double g_dt = 0;
+  float g_theta = -1, g_eps = -1;
+};
+
+// ------------------------------------------------------------ launches
+// k_build.cu
+cudaError_t launch_reset(Ctx &c, cudaStream_t s);
+cudaError_t launch_frame_keys(Ctx &c, const double *pos, const double *mass, cudaStream_t s);
+cudaError_t launch_sort(Ctx &c, cudaStream_t s);  // key[0]/idx[0] -> sorted key[0]/idx[0]
+cudaError_t launch_move(Ctx &c, const double *pos, const double *mass, cudaStream_t s);
+cudaError_t launch_move_state(Ctx &c, cudaStream_t s);  // gather state cur -> other, fills part_hi/lo
+cudaError_t launch_cells(Ctx &c, cudaStream_t s);
+cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+// k_moments.cu
+cudaError_t launch_moments(Ctx &c, cudaStream_t s);
+cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s);
+// k_walk.cu
+enum OutMode { kOutCaller = 0, kOutSorted = 1 };
+cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s);
+int walk_smem_bytes(int warps);
+cudaError_t walk_init_attrs(int smem);
+cudaError_t build_init_attrs();
+int walk_max_blocks_per_sm(int warps, int smem);
+// k_integrate.cu
+cudaError_t launch_predict(Ctx &c, double dt, cudaStream_t s);
+cudaError_t launch_correct(Ctx &c, double dt, cudaStream_t s);
+cudaError_t launch_load_state(Ctx &c, const double *pos, const double *vel, const double *mass, cudaStream_t s);
+cudaError_t launch_get_state(Ctx &c, double *pos, double *vel, float *acc, float *pot, cudaStream_t s);
+cudaError_t launch_diag(Ctx &c, cudaStream_t s);
+cudaError_t launch_fma_probe(int blocks, int threads, int iters, float *sink, cudaStream_t s);
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Index of the system holding sorted/input position i: last s with offs[s] <= i.
+__device__ __forceinline__ int sys_of(const int32_t *offs, int S, int i) {
+  int lo = 0, hi = S - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(offs + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Common prefix of two 60-bit keys, in levels (0..20).
+__device__ __forceinline__ int key_lcp(uint64_t a, uint64_t b) {
+  uint64_t x = a ^ b;
+  if (x == 0) return kLevels;
+  int h = 63 - __clzll((long long)x);
+  return (59 - h) / 3;
+}
+
+// Keep the low 20 bits of v, bit b moved to bit 3b (a 60-bit spread).
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+  uint64_t x = v & 0xfffffu;
+  x = (x | (x << 32)) & 0x001f00000000ffffull;
+  x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+// Inverse of spread3: bits 0, 3, 6, ... of x gathered into the low 20 bits.
+__device__ __forceinline__ uint32_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+  x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+  x = (x ^ (x >> 8)) & 0x001f0000ff0000ffull;
+  x = (x ^ (x >> 16)) & 0x001f00000000ffffull;
+  x = (x ^ (x >> 32)) & 0x00000000001fffffull;
+  return (uint32_t)x;
+}
+
+// FP64 value split into two floats: hi = rn(x), lo = rn(x - hi).
+__device__ __forceinline__ void split2(double x, float &hi, float &lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(__dsub_rn(x, (double)hi));
+}
+
+}  // namespace bh

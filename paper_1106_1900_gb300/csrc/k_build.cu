@@ -1,0 +1,842 @@
+// k_build.cu -- tree construction on the GPU (§2.1, App. A, App. B).
+//
+//  frame + keys   per-system bounding box (order-preserving 64-bit atomics),
+//                 frame (origin, power-of-two side L), 60-bit Morton keys.
+//  sort           stable LSD radix sort of (key, index), 8-bit digits, one
+//                 upsweep histogram for all passes and one pass kernel per
+//                 digit with decoupled look-back (bounded waits).  A forest
+//                 adds digits of the system id as the most significant ones.
+//  move           gather of the bodies into key order, split into two floats.
+//  cells          the paper's level loop (mask keys of unfinished bodies,
+//                 group equal masked keys, cells of <= N_leaf bodies become
+//                 leaves) computed for all 21 levels at once: a body's cell at
+//                 level k holds more than N bodies iff some run of N+1
+//                 consecutive sorted keys around it shares k levels, so each
+//                 body learns its leaf level from a sliding window over its
+//                 neighbours; the levels at which it starts a cell follow from
+//                 its common prefix with the previous key.  One prefix sum over
+//                 per-warp, per-level counts places every cell in (level, key)
+//                 order and every group in body order; links come from binary
+//                 searches in the sorted keys and the level-ordered cells.
+#include <cuda_runtime.h>
+
+#include "bh_internal.cuh"
+
+namespace bh {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ unsigned long long ord_of(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double double_of(unsigned long long o) {
+  unsigned long long b = (o >> 63) ? (o & 0x7fffffffffffffffull) : ~o;
+  return __longlong_as_double((long long)b);
+}
+
+// --------------------------------------------------------------- reset
+__global__ void k_reset(unsigned long long *minmax, int S, uint32_t *ticket) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 6 * S) minmax[t] = (t % 6 < 3) ? ~0ull : 0ull;
+  if (t == 0) *ticket = 0;
+}
+
+// ---------------------------------------------------- bounding box + frame
+// Each block reduces 4*256 consecutive bodies; a warp whose bodies share one
+// system reduces in registers, otherwise its lanes update the system directly.
+// The last block to finish turns min/max into the frame of every system.
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos, const double *__restrict__ mass,
+                                                 int n, const int32_t *__restrict__ offs, int S,
+                                                 unsigned long long *minmax, uint32_t *ticket, Frame *frame,
+                                                 int32_t *status) {
+  __shared__ double s_v[kBlock / 32][6];
+  __shared__ int s_sys[kBlock / 32];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int base = blockIdx.x * (4 * kBlock);
+  double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  int my_sys = -1;
+  bool bad = false, mixed = false;
+  for (int j = 0; j < 4; ++j) {
+    int i = base + threadIdx.x + j * kBlock;
+    if (i >= n) break;
+    double x0 = pos[3 * (size_t)i], x1 = pos[3 * (size_t)i + 1], x2 = pos[3 * (size_t)i + 2];
+    double m = mass[i];
+    bad |= !(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(m));
+    int s = FOREST ? sys_of(offs, S, i) : 0;
+    if (my_sys >= 0 && s != my_sys) {
+      // body of another system: flush what we have and start again
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&minmax[6 * my_sys + a], ord_of(v[a]));
+        atomicMax(&minmax[6 * my_sys + 3 + a], ord_of(v[3 + a]));
+      }
+      v[0] = v[1] = v[2] = INFINITY;
+      v[3] = v[4] = v[5] = -INFINITY;
+      mixed = true;
+    }
+    my_sys = s;
+    v[0] = fmin(v[0], x0); v[1] = fmin(v[1], x1); v[2] = fmin(v[2], x2);
+    v[3] = fmax(v[3], x0); v[4] = fmax(v[4], x1); v[5] = fmax(v[5], x2);
+  }
+  (void)mixed;
+  if (bad) set_status(status, BH_ERR_NONFINITE);
+  int s0 = __shfl_sync(kFull, my_sys, 0);
+  bool uniform = __all_sync(kFull, my_sys == s0 || my_sys < 0) && s0 >= 0;
+  if (uniform) {
+    for (int o = 16; o > 0; o >>= 1)
+      for (int a = 0; a < 3; ++a) {
+        v[a] = fmin(v[a], __shfl_xor_sync(kFull, v[a], o));
+        v[3 + a] = fmax(v[3 + a], __shfl_xor_sync(kFull, v[3 + a], o));
+      }
+    if (lane == 0) {
+      for (int a = 0; a < 6; ++a) s_v[warp][a] = v[a];
+      s_sys[warp] = s0;
+    }
+  } else {
+    if (my_sys >= 0)
+      for (int a = 0; a < 3; ++a) {
+        atomicMin(&minmax[6 * my_sys + a], ord_of(v[a]));
+        atomicMax(&minmax[6 * my_sys + 3 + a], ord_of(v[3 + a]));
+      }
+    if (lane == 0) s_sys[warp] = -1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // merge the warps' partials, one set of atomics per run of equal systems
+    int cur = -1;
+    double acc[6];
+    for (int w = 0; w <= kBlock / 32; ++w) {
+      int s = (w < kBlock / 32) ? s_sys[w] : -2;
+      if (s != cur && cur >= 0) {
+        for (int a = 0; a < 3; ++a) {
+          atomicMin(&minmax[6 * cur + a], ord_of(acc[a]));
+          atomicMax(&minmax[6 * cur + 3 + a], ord_of(acc[3 + a]));
+        }
+        cur = -1;
+      }
+      if (s >= 0) {
+        if (cur < 0) {
+          cur = s;
+          for (int a = 0; a < 6; ++a) acc[a] = s_v[w][a];
+        } else {
+          for (int a = 0; a < 3; ++a) {
+            acc[a] = fmin(acc[a], s_v[w][a]);
+            acc[3 + a] = fmax(acc[3 + a], s_v[w][3 + a]);
+          }
+        }
+      }
+    }
+    __threadfence();
+    s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    Frame f = {0.0, 0.0, 0.0, 1.0};
+    if (offs[s + 1] > offs[s]) {
+      double lo[3], hi[3];
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = double_of(__ldcg(&minmax[6 * s + a]));
+        hi[a] = double_of(__ldcg(&minmax[6 * s + 3 + a]));
+      }
+      double E = 0.0;
+      for (int a = 0; a < 3; ++a) E = fmax(E, __dsub_rn(hi[a], lo[a]));
+      double L = 1.0;
+      if (E > 0.0) {
+        double v2 = __dmul_rn(E, 1.0 + 0x1p-20);
+        int e;
+        double m = frexp(v2, &e);
+        L = (m == 0.5) ? v2 : ldexp(1.0, e);
+      }
+      f = Frame{lo[0], lo[1], lo[2], L};
+    }
+    frame[s] = f;
+  }
+  if (threadIdx.x == 0) *ticket = 0;
+}
+
+// ----------------------------------------------------------------- keys
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos, int n,
+                                                 const int32_t *__restrict__ offs, int S,
+                                                 const Frame *__restrict__ frame, uint64_t *__restrict__ key,
+                                                 uint32_t *__restrict__ idx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = FOREST ? sys_of(offs, S, i) : 0;
+  Frame f = frame[s];
+  double scale = __ddiv_rn((double)kQMax, f.w);  // exact: both are powers of two
+  double o[3] = {f.x, f.y, f.z};
+  uint32_t q[3];
+  for (int a = 0; a < 3; ++a) {
+    double t = floor(__dmul_rn(__dsub_rn(pos[3 * (size_t)i + a], o[a]), scale));
+    t = fmin(fmax(t, 0.0), (double)(kQMax - 1));
+    q[a] = (uint32_t)t;
+  }
+  key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  idx[i] = (uint32_t)i;
+}
+
+// ----------------------------------------------------------------- sort
+constexpr int kSortIpt = 16;
+constexpr int kSortTile = kBlock * kSortIpt;
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t sort_digit(uint64_t k, uint32_t v, int pass, int key_passes,
+                                               const int32_t *offs, int S) {
+  if (pass < key_passes) return (uint32_t)(k >> (8 * pass)) & 0xffu;
+  return ((uint32_t)sys_of(offs, S, (int)v) >> (8 * (pass - key_passes))) & 0xffu;
+}
+
+// All digit histograms in one read of the keys.
+__global__ void __launch_bounds__(kBlock) k_sort_hist(const uint64_t *__restrict__ key, int n, int passes,
+                                                      int key_passes, const int32_t *__restrict__ offs, int S,
+                                                      uint32_t *hist) {
+  extern __shared__ uint32_t s_h[];  // [passes][256]
+  for (int t = threadIdx.x; t < passes * 256; t += blockDim.x) s_h[t] = 0;
+  __syncthreads();
+  const unsigned lane_lt = lanemask_lt();
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    int i = base + threadIdx.x;
+    bool ok = i < n;
+    uint64_t k = ok ? key[i] : 0;
+    for (int p = 0; p < passes; ++p) {
+      uint32_t d = ok ? sort_digit(k, (uint32_t)i, p, key_passes, offs, S) : 256u;
+      unsigned peers = __match_any_sync(kFull, d);
+      if (ok && (peers & lane_lt) == 0) atomicAdd(&s_h[p * 256 + d], __popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < passes * 256; t += blockDim.x)
+    if (s_h[t]) atomicAdd(&hist[t], s_h[t]);
+}
+
+// Exclusive prefix of each pass's 256 bins (one block per pass).
+__global__ void k_sort_binscan(uint32_t *hist) {
+  __shared__ uint32_t s[256];
+  uint32_t *h = hist + blockIdx.x * 256;
+  s[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int d = 0; d < 256; ++d) {
+      uint32_t c = s[d];
+      s[d] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  h[threadIdx.x] = s[threadIdx.x];
+}
+
+// 256-thread exclusive scan helper; returns the exclusive prefix of v.
+__device__ __forceinline__ uint32_t block256_exclusive(uint32_t v, uint32_t *s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < 8) ? s_warp[lane] : 0;
+    for (int o = 1; o < 8; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < 8) s_warp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t before = (warp > 0) ? s_warp[warp - 1] : 0;
+  __syncthreads();
+  return before + x - v;
+}
+
+// One stable digit pass.  Tiles are taken in launch order from a counter, so
+// every tile's predecessors are already running; each tile publishes its
+// digit counts, then sums its predecessors' (bounded wait), then scatters.
+__global__ void __launch_bounds__(kBlock) k_sort_pass(const uint64_t *__restrict__ kin,
+                                                      const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+                                                      uint32_t *__restrict__ vout, int n, int pass, int key_passes,
+                                                      const uint32_t *__restrict__ binbase, uint32_t *status,
+                                                      uint32_t *tile_ctr, const int32_t *__restrict__ offs, int S,
+                                                      int32_t *err) {
+  __shared__ uint32_t s_wcnt[kBlock / 32][256];
+  __shared__ uint32_t s_tstart[256];
+  __shared__ uint32_t s_gbase[256];
+  __shared__ uint32_t s_scan[8];
+  __shared__ uint32_t s_tile;
+  extern __shared__ unsigned char s_dyn[];
+  uint64_t *s_k = reinterpret_cast<uint64_t *>(s_dyn);
+  uint32_t *s_v = reinterpret_cast<uint32_t *>(s_k + kSortTile);
+  uint8_t *s_d = reinterpret_cast<uint8_t *>(s_v + kSortTile);
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  for (int t = threadIdx.x; t < (kBlock / 32) * 256; t += kBlock) (&s_wcnt[0][0])[t] = 0;
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const int base = (int)tile * kSortTile;
+  const int tile_n = min(kSortTile, n - base);
+
+  uint64_t k[kSortIpt];
+  uint32_t v[kSortIpt], d[kSortIpt], r[kSortIpt];
+  const unsigned lt = lanemask_lt();
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    int e = base + warp * 32 * kSortIpt + j * 32 + lane;
+    bool ok = e < n;
+    k[j] = ok ? kin[e] : 0;
+    v[j] = ok ? vin[e] : 0;
+    d[j] = ok ? sort_digit(k[j], v[j], pass, key_passes, offs, S) : 256u;
+  }
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    unsigned peers = __match_any_sync(kFull, d[j]);
+    uint32_t cnt = (d[j] < 256) ? s_wcnt[warp][d[j]] : 0;
+    r[j] = cnt + __popc(peers & lt);
+    __syncwarp();
+    if (d[j] < 256 && (peers & lt) == 0) s_wcnt[warp][d[j]] = cnt + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // digit t: per-warp exclusive offsets and the tile's count
+  const int t = threadIdx.x;
+  uint32_t tot = 0;
+  for (int w = 0; w < kBlock / 32; ++w) {
+    uint32_t c = s_wcnt[w][t];
+    s_wcnt[w][t] = tot;
+    tot += c;
+  }
+  uint32_t *my = status + (size_t)tile * 256;
+  if (tile == 0) atomicExch(&my[t], kFlagInc | tot);
+  else atomicExch(&my[t], kFlagAgg | tot);
+  uint32_t tstart = block256_exclusive(tot, s_scan);
+  s_tstart[t] = tstart;
+  uint32_t excl = 0;
+  if (tile > 0) {
+    int pr = (int)tile - 1;
+    int spins = 0;
+    while (pr >= 0) {
+      uint32_t w = __ldcv(&status[(size_t)pr * 256 + t]);
+      if ((w & ~kValMask) == 0) {
+        if (++spins > kSpinLimit) {
+          set_status(err, BH_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(32);
+        continue;
+      }
+      excl += w & kValMask;
+      if ((w & ~kValMask) == kFlagInc) break;
+      --pr;
+    }
+    atomicExch(&my[t], kFlagInc | (excl + tot));
+  }
+  s_gbase[t] = binbase[t] + excl;
+  __syncthreads();
+  // scatter into shared memory in (digit, arrival) order
+#pragma unroll
+  for (int j = 0; j < kSortIpt; ++j) {
+    if (d[j] < 256) {
+      uint32_t lp = s_tstart[d[j]] + s_wcnt[warp][d[j]] + r[j];
+      s_k[lp] = k[j];
+      s_v[lp] = v[j];
+      s_d[lp] = (uint8_t)d[j];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tile_n; e += kBlock) {
+    uint32_t dd = s_d[e];
+    uint32_t g = s_gbase[dd] + ((uint32_t)e - s_tstart[dd]);
+    kout[g] = s_k[e];
+    vout[g] = s_v[e];
+  }
+}
+
+// ----------------------------------------------------------------- move
+__global__ void __launch_bounds__(kBlock) k_move(const double *__restrict__ pos, const double *__restrict__ mass,
+                                                 const uint32_t *__restrict__ perm, int n, float4 *part_hi,
+                                                 float4 *part_lo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  size_t j = perm[i];
+  float h[3], l[3];
+  for (int a = 0; a < 3; ++a) split2(pos[3 * j + a], h[a], l[a]);
+  part_hi[i] = make_float4(h[0], h[1], h[2], (float)mass[j]);
+  part_lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// Gather of the integrator state into the new key order (+ the two-float bodies).
+__global__ void __launch_bounds__(kBlock) k_move_state(const uint32_t *__restrict__ perm, int n,
+                                                       const double *__restrict__ x0, const double *__restrict__ v0,
+                                                       const double *__restrict__ m0, const float4 *__restrict__ a0,
+                                                       const int32_t *__restrict__ id0, double *x1, double *v1,
+                                                       double *m1, float4 *a1, int32_t *id1, float4 *part_hi,
+                                                       float4 *part_lo) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  size_t j = perm[i];
+  float h[3], l[3];
+  for (int a = 0; a < 3; ++a) {
+    double x = x0[3 * j + a];
+    x1[3 * (size_t)i + a] = x;
+    v1[3 * (size_t)i + a] = v0[3 * j + a];
+    split2(x, h[a], l[a]);
+  }
+  double m = m0[j];
+  m1[i] = m;
+  a1[i] = a0[j];
+  id1[i] = id0[j];
+  part_hi[i] = make_float4(h[0], h[1], h[2], (float)m);
+  part_lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// ---------------------------------------------------------------- cells
+constexpr int kHalo = 64;  // >= N_crit >= N_leaf
+
+// Per body: first level it starts a cell at (common prefix with the previous
+// key + 1), its leaf level, whether it starts a group; per warp: how many
+// cells it starts at each level and how many groups.
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ skey, int n,
+                                                   const int32_t *__restrict__ offs, int S, int n_leaf, int n_crit,
+                                                   uint8_t *lohi, uint8_t *gstart, uint32_t *rowcnt, int W) {
+  __shared__ uint64_t s_key[kBlock + 2 * kHalo];
+  __shared__ int8_t s_wl[kBlock + kHalo];  // lcp of windows of N_leaf + 1 keys starting at b0 - kHalo + t
+  __shared__ int8_t s_wc[kBlock + kHalo];  // lcp of windows of N_crit + 1 keys
+  const int b0 = blockIdx.x * kBlock;
+  for (int t = threadIdx.x; t < kBlock + 2 * kHalo; t += kBlock) {
+    int i = b0 - kHalo + t;
+    s_key[t] = (i >= 0 && i < n) ? skey[i] : 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < kBlock + kHalo; t += kBlock) {
+    int s0 = b0 - kHalo + t;  // window start
+    int8_t wl = -1, wc = -1;
+    if (s0 >= 0 && s0 < n) {
+      int sb = 0, se = n;
+      if (FOREST) {
+        int s = sys_of(offs, S, s0);
+        sb = offs[s];
+        se = offs[s + 1];
+      }
+      (void)sb;
+      if (s0 + n_leaf < se) wl = (int8_t)key_lcp(s_key[t], s_key[t + n_leaf]);
+      if (s0 + n_crit < se) wc = (int8_t)key_lcp(s_key[t], s_key[t + n_crit]);
+    }
+    s_wl[t] = wl;
+    s_wc[t] = wc;
+  }
+  __syncthreads();
+  const int i = b0 + threadIdx.x;
+  const bool ok = i < n;
+  int lo = 1, hi = 0, gs = 0;
+  if (ok) {
+    int sb = 0;
+    if (FOREST) sb = offs[sys_of(offs, S, i)];
+    const int t = threadIdx.x + kHalo;  // position of i in s_key
+    int prev = (i > sb) ? key_lcp(s_key[t - 1], s_key[t]) : -1;
+    // windows of N+1 keys starting at i-N .. i (a window's lcp is -1 where it leaves the system)
+    int wl = -1, wc = -1;
+    for (int q = 0; q <= n_leaf; ++q) {
+      if (i - q < sb) break;
+      wl = max(wl, (int)s_wl[threadIdx.x + kHalo - q]);
+    }
+    for (int q = 0; q <= n_crit; ++q) {
+      if (i - q < sb) break;
+      wc = max(wc, (int)s_wc[threadIdx.x + kHalo - q]);
+    }
+    int lam = min(wl + 1, kLevels);
+    int mu = wc + 1;  // 21: even the level-20 cell holds more than N_crit bodies
+    lo = prev + 1;
+    hi = lam;
+    if (mu <= lam) {
+      gs = (lo <= mu);
+    } else {
+      // chunks of N_crit inside a level-20 leaf: find the start of the run of equal keys
+      uint64_t kk = s_key[t];
+      int a = sb, b = i;  // first index in [a, b] with key == kk
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        if (skey[mid] < kk) a = mid + 1; else b = mid;
+      }
+      gs = ((i - a) % n_crit) == 0;
+    }
+    lohi[2 * (size_t)i] = (uint8_t)lo;
+    lohi[2 * (size_t)i + 1] = (uint8_t)hi;
+    gstart[i] = (uint8_t)gs;
+  }
+  const int lane = threadIdx.x & 31;
+  const int w = i >> 5;
+  uint32_t mine = 0;
+#pragma unroll
+  for (int k = 0; k <= kLevels; ++k) {
+    unsigned b = __ballot_sync(kFull, ok && lo <= k && k <= hi);
+    if (lane == k) mine = __popc(b);
+  }
+  unsigned bg = __ballot_sync(kFull, ok && gs);
+  if (lane == kRows - 1) mine = __popc(bg);
+  if (lane < kRows && w < W) rowcnt[(size_t)lane * W + w] = mine;
+}
+
+// Writes every cell (level, leaf flag, first body, parent/first child where
+// the same body starts both) and every group start.
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_emit(int n, const int32_t *__restrict__ offs, int S,
+                                                 const uint8_t *__restrict__ lohi, const uint8_t *__restrict__ gstart,
+                                                 const uint32_t *__restrict__ rowoff, int W,
+                                                 const uint64_t *__restrict__ scan_total, int32_t *c_level,
+                                                 int32_t *c_pbeg, int32_t *c_parent, int32_t *c_first,
+                                                 uint32_t *c_ctr, int32_t *sys_root, int32_t *g_beg, int32_t *g_sys,
+                                                 int32_t *counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int w = i >> 5;
+  const bool ok = i < n;
+  const unsigned lt = lanemask_lt();
+  int lo = 1, hi = 0, gs = 0, s = 0;
+  if (ok) {
+    lo = lohi[2 * (size_t)i];
+    hi = lohi[2 * (size_t)i + 1];
+    gs = gstart[i];
+    if (FOREST) s = sys_of(offs, S, i);
+  }
+  const uint32_t C = rowoff[(size_t)(kRows - 1) * W];
+  int prev = -1;
+  for (int k = 0; k <= kLevels; ++k) {
+    bool in = ok && lo <= k && k <= hi;
+    unsigned b = __ballot_sync(kFull, in);
+    if (b == 0) continue;
+    if (in) {
+      int cell = (int)(rowoff[(size_t)k * W + w] + __popc(b & lt));
+      bool leaf = (k == hi);
+      c_level[cell] = k | (leaf ? 32 : 0);
+      c_pbeg[cell] = i;
+      c_parent[cell] = (k > lo) ? prev : -1;
+      c_first[cell] = -1;
+      c_ctr[cell] = 0;
+      if (k > lo) c_first[prev] = cell;
+      if (k == 0) sys_root[s] = cell;
+      prev = cell;
+    }
+  }
+  unsigned bg = __ballot_sync(kFull, ok && gs);
+  if (ok && gs) {
+    int g = (int)(rowoff[(size_t)(kRows - 1) * W + w] - C + __popc(bg & lt));
+    g_beg[g] = i;
+    g_sys[g] = s;
+  }
+  if (i == 0) {
+    uint32_t G = (uint32_t)(*scan_total) - C;
+    counts[0] = (int32_t)C;
+    counts[1] = (int32_t)G;
+    g_beg[G] = n;
+  }
+}
+
+// One thread per cell: body range end (galloping search in the sorted keys),
+// parent (binary search among the cells one level up), number of children
+// (binary search among the cells one level down) and the walk's link word.
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_link(int n, const uint64_t *__restrict__ skey,
+                                                 const int32_t *__restrict__ offs, int S,
+                                                 const uint32_t *__restrict__ rowoff, int W,
+                                                 const int32_t *__restrict__ counts, int32_t *c_level,
+                                                 const int32_t *__restrict__ c_pbeg, int32_t *c_pend,
+                                                 int32_t *c_parent, const int32_t *__restrict__ c_first,
+                                                 int32_t *c_nch, int2 *c_link) {
+  const int C = counts[0];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const int lv = c_level[c];
+    const int k = lv & 31;
+    const bool leaf = lv & 32;
+    const int i = c_pbeg[c];
+    int se = n;
+    if (FOREST) se = offs[sys_of(offs, S, i) + 1];
+    int pend = se;
+    if (k > 0) {
+      const int sh = 60 - 3 * k;
+      const uint64_t P = skey[i] >> sh;
+      int in_run = i, step = 1;
+      while (i + step < se && (skey[i + step] >> sh) == P) {
+        in_run = i + step;
+        step <<= 1;
+      }
+      int a = in_run + 1, b = min(i + step, se);  // first index with another prefix lies in [a, b]
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        if ((skey[mid] >> sh) == P) a = mid + 1; else b = mid;
+      }
+      pend = a;
+    }
+    c_pend[c] = pend;
+    int par = c_parent[c];
+    if (k > 0 && par < 0) {
+      int a = (int)rowoff[(size_t)(k - 1) * W], b = (int)rowoff[(size_t)k * W] - 1;  // last cell with pbeg <= i
+      while (a < b) {
+        int mid = (a + b + 1) >> 1;
+        if (c_pbeg[mid] <= i) a = mid; else b = mid - 1;
+      }
+      par = a;
+      c_parent[c] = par;
+    }
+    int nch = 0;
+    if (!leaf) {
+      const int f = c_first[c];
+      int a = f, b = (int)rowoff[(size_t)(k + 2) * W];  // first level-(k+1) cell with pbeg >= pend
+      while (a < b) {
+        int mid = (a + b) >> 1;
+        if (c_pbeg[mid] < pend) a = mid + 1; else b = mid;
+      }
+      nch = a - f;
+      c_link[c] = make_int2(f, nch);
+    } else {
+      c_link[c] = make_int2(i, (int)((unsigned)(pend - i) | 0x80000000u));
+    }
+    c_nch[c] = nch;
+  }
+}
+
+// ----------------------------------------------------------------- scan
+constexpr int kScanIpt = 16;
+constexpr int kScanTile = kBlock * kScanIpt;
+
+__global__ void __launch_bounds__(kBlock) k_scan_up(const uint32_t *__restrict__ in, int64_t n, uint32_t *blocks) {
+  __shared__ uint32_t s_w[kBlock / 32];
+  const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
+  uint32_t sum = 0;
+  for (int j = 0; j < kScanIpt; ++j) {
+    int64_t i = b0 + j * kBlock + threadIdx.x;
+    if (i < n) sum += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < kBlock / 32; ++w) t += s_w[w];
+    blocks[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_mid(uint32_t *blocks, int nb, uint64_t *total) {
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    uint32_t v = (i < nb) ? blocks[i] : 0;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_w[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(kFull, w, o);
+        if (lane >= o) w += y;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    uint32_t carry = s_carry;
+    uint32_t excl = carry + (warp ? s_w[warp - 1] : 0) + x - v;
+    if (i < nb) blocks[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + s_w[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = s_carry;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_down(const uint32_t *__restrict__ in, int64_t n,
+                                                      const uint32_t *__restrict__ blocks, uint32_t *out) {
+  __shared__ uint32_t s[kScanTile];
+  __shared__ uint32_t s_w[kBlock / 32];
+  const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
+  for (int j = 0; j < kScanIpt; ++j) {
+    int64_t i = b0 + j * kBlock + threadIdx.x;
+    s[j * kBlock + threadIdx.x] = (i < n) ? in[i] : 0;
+  }
+  __syncthreads();
+  uint32_t loc[kScanIpt];
+  uint32_t sum = 0;
+  for (int j = 0; j < kScanIpt; ++j) {
+    loc[j] = sum;
+    sum += s[threadIdx.x * kScanIpt + j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  uint32_t wb = 0;
+  for (int w = 0; w < warp; ++w) wb += s_w[w];
+  const uint32_t base = blocks[blockIdx.x] + wb + x - sum;
+  __syncthreads();
+  for (int j = 0; j < kScanIpt; ++j) s[threadIdx.x * kScanIpt + j] = base + loc[j];
+  __syncthreads();
+  for (int j = 0; j < kScanIpt; ++j) {
+    int64_t i = b0 + j * kBlock + threadIdx.x;
+    if (i < n) out[i] = s[j * kBlock + threadIdx.x];
+  }
+}
+
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+// =================================================================== launches
+cudaError_t launch_reset(Ctx &c, cudaStream_t s) {
+  int n = 6 * c.n_sys;
+  k_reset<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.minmax, c.n_sys, c.frame_ticket);
+  c.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_frame_keys(Ctx &c, const double *pos, const double *mass, cudaStream_t s) {
+  const int n = (int)c.n;
+  const bool forest = c.n_sys > 1;
+  int nb = cdiv(n, 4 * kBlock);
+  if (forest)
+    k_bbox<true><<<nb, kBlock, 0, s>>>(pos, mass, n, c.offs, c.n_sys, c.minmax, c.frame_ticket, c.frame, c.d_status);
+  else
+    k_bbox<false><<<nb, kBlock, 0, s>>>(pos, mass, n, c.offs, c.n_sys, c.minmax, c.frame_ticket, c.frame,
+                                        c.d_status);
+  if (forest)
+    k_keys<true><<<cdiv(n, kBlock), kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, c.key[0], c.idx[0]);
+  else
+    k_keys<false><<<cdiv(n, kBlock), kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, c.key[0], c.idx[0]);
+  c.launches += 2;
+  return cudaGetLastError();
+}
+
+static int sort_sys_passes(int S) {
+  if (S <= 1) return 0;
+  int bits = 0;
+  while ((1 << bits) < S) ++bits;
+  return (bits + 7) / 8;
+}
+
+int sort_passes_for(int S) { return 8 + sort_sys_passes(S); }
+
+cudaError_t build_init_attrs() {
+  return cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)((size_t)kSortTile * (8 + 4 + 1)));
+}
+int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
+  const int n = (int)c.n;
+  const int key_passes = 8;
+  const int passes = key_passes + sort_sys_passes(c.n_sys);
+  const int tiles = cdiv(n, kSortTile);
+  cudaError_t e;
+  e = cudaMemsetAsync(c.sort_hist, 0, sizeof(uint32_t) * passes * 256, s);
+  if (e) return e;
+  e = cudaMemsetAsync(c.sort_status, 0, sizeof(uint32_t) * (size_t)passes * tiles * 256, s);
+  if (e) return e;
+  e = cudaMemsetAsync(c.sort_tile_ctr, 0, sizeof(uint32_t) * passes, s);
+  if (e) return e;
+  int hb = min(cdiv(n, kBlock), c.num_sms * 4);
+  k_sort_hist<<<hb, kBlock, sizeof(uint32_t) * passes * 256, s>>>(c.key[0], n, passes, key_passes, c.offs,
+                                                                   c.n_sys, c.sort_hist);
+  k_sort_binscan<<<passes, 256, 0, s>>>(c.sort_hist);
+  const size_t dyn = (size_t)kSortTile * (8 + 4 + 1);
+  for (int p = 0; p < passes; ++p) {
+    int src = p & 1;
+    k_sort_pass<<<tiles, kBlock, dyn, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1], n, p, key_passes,
+                                           c.sort_hist + p * 256, c.sort_status + (size_t)p * tiles * 256,
+                                           c.sort_tile_ctr + p, c.offs, c.n_sys, c.d_status);
+  }
+  c.launches += 2 + passes;
+  if (passes & 1) {  // 9 passes (forest of 2..256 systems): bring the result back to buffer 0
+    e = cudaMemcpyAsync(c.key[0], c.key[1], sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e) return e;
+    e = cudaMemcpyAsync(c.idx[0], c.idx[1], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+    if (e) return e;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move(Ctx &c, const double *pos, const double *mass, cudaStream_t s) {
+  const int n = (int)c.n;
+  k_move<<<cdiv(n, kBlock), kBlock, 0, s>>>(pos, mass, c.idx[0], n, c.part_hi, c.part_lo);
+  c.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_move_state(Ctx &c, cudaStream_t s) {
+  const int n = (int)c.n;
+  const int a = c.state_cur, b = a ^ 1;
+  k_move_state<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.idx[0], n, c.st_x[a], c.st_v[a], c.st_m[a], c.st_a[a],
+                                                  c.st_id[a], c.st_x[b], c.st_v[b], c.st_m[b], c.st_a[b],
+                                                  c.st_id[b], c.part_hi, c.part_lo);
+  c.state_cur = b;
+  c.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s) {
+  int nb = cdiv(n, kScanTile);
+  if (nb == 0) {
+    c.launches++;
+    return cudaMemsetAsync(c.scan_total, 0, sizeof(uint64_t), s);
+  }
+  k_scan_up<<<nb, kBlock, 0, s>>>(in, n, c.scan_blocks);
+  k_scan_mid<<<1, 1024, 0, s>>>(c.scan_blocks, nb, c.scan_total);
+  k_scan_down<<<nb, kBlock, 0, s>>>(in, n, c.scan_blocks, out);
+  c.launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cells(Ctx &c, cudaStream_t s) {
+  const int n = (int)c.n;
+  const int W = cdiv(n, 32);
+  const bool forest = c.n_sys > 1;
+  const int nb = cdiv(n, kBlock);
+  if (forest)
+    k_levels<true><<<nb, kBlock, 0, s>>>(c.key[0], n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit, c.lohi, c.gstart,
+                                         c.rowcnt, W);
+  else
+    k_levels<false><<<nb, kBlock, 0, s>>>(c.key[0], n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit, c.lohi, c.gstart,
+                                          c.rowcnt, W);
+  c.launches++;
+  cudaError_t e = launch_scan_u32(c, c.rowcnt, c.rowoff, (int64_t)kRows * W, s);
+  if (e) return e;
+  if (forest)
+    k_emit<true><<<nb, kBlock, 0, s>>>(n, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total, c.c_level,
+                                       c.c_pbeg, c.c_parent, c.c_first, c.c_ctr, c.sys_root, c.g_beg, c.g_sys,
+                                       c.d_counts);
+  else
+    k_emit<false><<<nb, kBlock, 0, s>>>(n, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total, c.c_level,
+                                        c.c_pbeg, c.c_parent, c.c_first, c.c_ctr, c.sys_root, c.g_beg, c.g_sys,
+                                        c.d_counts);
+  const int lb = c.num_sms * 8;
+  if (forest)
+    k_link<true><<<lb, kBlock, 0, s>>>(n, c.key[0], c.offs, c.n_sys, c.rowoff, W, c.d_counts, c.c_level, c.c_pbeg,
+                                       c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_link);
+  else
+    k_link<false><<<lb, kBlock, 0, s>>>(n, c.key[0], c.offs, c.n_sys, c.rowoff, W, c.d_counts, c.c_level, c.c_pbeg,
+                                        c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_link);
+  c.launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace bh

@@ -1,0 +1,216 @@
+// k_moments.cu -- monopole + quadrupole moments of every cell (§3.2, Fig. 4).
+//
+// The paper computes the leaves in parallel and then the nodes level by
+// level, bottom to top, from the moments one level below.  Here the same
+// bottom-up order runs in one launch: every leaf computes its moments from
+// its bodies, then climbs; a node is computed by whichever child arrives
+// last at its counter (the others stop), from all its children in index
+// order, so the result does not depend on arrival order.  Nothing waits.
+//
+// Arithmetic is FP32 in cell-relative coordinates (the paper uses FP64 on
+// hardware whose FP32 path lost accuracy in absolute coordinates): a body
+// offset from the cell's geometric centre is (x_hi - c_hi) + (x_lo - c_lo)
+// from the two-float forms of both; children's centres of mass enter the
+// parent through the parallel-axis shift.
+//
+// Record per cell (4 x float4):
+//   mom[4c+0] = (com_hi.x, com_hi.y, com_hi.z, M)
+//   mom[4c+1] = (com_lo.x, com_lo.y, com_lo.z, delta = |com - centre|)
+//   mom[4c+2] = (Qxx, Qyy, Qzz, Qxy)
+//   mom[4c+3] = (Qxz, Qyz, l, 0)         Q = sum m (3 r r^T - r^2 I) about com
+#include <cuda_runtime.h>
+
+#include "bh_internal.cuh"
+
+namespace bh {
+namespace {
+
+constexpr int kBlock = 256;
+
+struct Centre {
+  double c[3];
+  float hi[3], lo[3];
+  float l;
+};
+
+// Geometric centre origin + (i + 1/2) l of the level-k cell holding sorted body i.
+template <bool FOREST>
+__device__ __forceinline__ Centre cell_centre(int k, int i, const uint64_t *__restrict__ skey,
+                                              const int32_t *__restrict__ offs, int S,
+                                              const Frame *__restrict__ frame) {
+  int s = FOREST ? sys_of(offs, S, i) : 0;
+  Frame f = frame[s];
+  double l = ldexp(f.w, -k);
+  uint64_t key = skey[i];
+  double o[3] = {f.x, f.y, f.z};
+  Centre C;
+  for (int a = 0; a < 3; ++a) {
+    uint32_t corner = (k == 0) ? 0u : (compact3(key >> a) >> (kLevels - k));
+    C.c[a] = __dadd_rn(o[a], __dmul_rn((double)corner + 0.5, l));
+    split2(C.c[a], C.hi[a], C.lo[a]);
+  }
+  C.l = (float)l;
+  return C;
+}
+
+__device__ __forceinline__ void write_cell(float4 *mom, int c, const Centre &C, float M, const float cm[3],
+                                           const float Q[6]) {
+  float hi[3], lo[3];
+  for (int a = 0; a < 3; ++a) split2(__dadd_rn(C.c[a], (double)cm[a]), hi[a], lo[a]);
+  float delta = sqrtf(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]);
+  mom[4 * (size_t)c + 0] = make_float4(hi[0], hi[1], hi[2], M);
+  mom[4 * (size_t)c + 1] = make_float4(lo[0], lo[1], lo[2], delta);
+  mom[4 * (size_t)c + 2] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+  mom[4 * (size_t)c + 3] = make_float4(Q[4], Q[5], C.l, 0.f);
+}
+
+__device__ __forceinline__ void add_point_quad(float Q[6], float m, float dx, float dy, float dz) {
+  float r2 = dx * dx + dy * dy + dz * dz;
+  Q[0] += m * (3.f * dx * dx - r2);
+  Q[1] += m * (3.f * dy * dy - r2);
+  Q[2] += m * (3.f * dz * dz - r2);
+  Q[3] += m * 3.f * dx * dy;
+  Q[4] += m * 3.f * dx * dz;
+  Q[5] += m * 3.f * dy * dz;
+}
+
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__ skey,
+                                                    const int32_t *__restrict__ offs, int S,
+                                                    const Frame *__restrict__ frame,
+                                                    const int32_t *__restrict__ counts,
+                                                    const int32_t *__restrict__ c_level,
+                                                    const int32_t *__restrict__ c_pbeg,
+                                                    const int32_t *__restrict__ c_pend,
+                                                    const int32_t *__restrict__ c_parent,
+                                                    const int32_t *__restrict__ c_first,
+                                                    const int32_t *__restrict__ c_nch, uint32_t *c_ctr,
+                                                    const float4 *__restrict__ part_hi,
+                                                    const float4 *__restrict__ part_lo, float4 *mom) {
+  const int C = counts[0];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const int lv = c_level[c];
+    if (!(lv & 32)) continue;  // nodes are finished by their last child
+    // ---- leaf: from its bodies
+    {
+      const int k = lv & 31, b = c_pbeg[c], e = c_pend[c];
+      Centre G = cell_centre<FOREST>(k, b, skey, offs, S, frame);
+      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+      for (int i = b; i < e; ++i) {
+        float4 h = part_hi[i], l = part_lo[i];
+        float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]);
+        float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]);
+        float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]);
+        M += h.w;
+        sx += h.w * dx;
+        sy += h.w * dy;
+        sz += h.w * dz;
+      }
+      float cm[3] = {0.f, 0.f, 0.f};
+      if (M > 0.f) {
+        cm[0] = sx / M;
+        cm[1] = sy / M;
+        cm[2] = sz / M;
+      }
+      float Q[6] = {0, 0, 0, 0, 0, 0};
+      for (int i = b; i < e; ++i) {
+        float4 h = part_hi[i], l = part_lo[i];
+        float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]) - cm[0];
+        float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]) - cm[1];
+        float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]) - cm[2];
+        add_point_quad(Q, h.w, dx, dy, dz);
+      }
+      write_cell(mom, c, G, M, cm, Q);
+    }
+    // ---- climb while this thread is the last child to arrive
+    int cur = c;
+    for (int climb = 0; climb <= kLevels; ++climb) {  // at most 20 ancestors
+      const int p = c_parent[cur];
+      if (p < 0 || p >= C) break;
+      __threadfence();
+      const uint32_t nch = (uint32_t)c_nch[p];
+      if (nch == 0 || nch > 8) break;
+      if (atomicAdd(&c_ctr[p], 1u) != nch - 1) break;
+      __threadfence();
+      const int k = c_level[p] & 31;
+      Centre G = cell_centre<FOREST>(k, c_pbeg[p], skey, offs, S, frame);
+      const int f = c_first[p];
+      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+      for (uint32_t j = 0; j < nch; ++j) {
+        float4 a = __ldcg(&mom[4 * (size_t)(f + j)]);
+        float4 b = __ldcg(&mom[4 * (size_t)(f + j) + 1]);
+        float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]);
+        float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]);
+        float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]);
+        M += a.w;
+        sx += a.w * dx;
+        sy += a.w * dy;
+        sz += a.w * dz;
+      }
+      float cm[3] = {0.f, 0.f, 0.f};
+      if (M > 0.f) {
+        cm[0] = sx / M;
+        cm[1] = sy / M;
+        cm[2] = sz / M;
+      }
+      float Q[6] = {0, 0, 0, 0, 0, 0};
+      for (uint32_t j = 0; j < nch; ++j) {
+        float4 a = __ldcg(&mom[4 * (size_t)(f + j)]);
+        float4 b = __ldcg(&mom[4 * (size_t)(f + j) + 1]);
+        float4 q0 = __ldcg(&mom[4 * (size_t)(f + j) + 2]);
+        float4 q1 = __ldcg(&mom[4 * (size_t)(f + j) + 3]);
+        float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]) - cm[0];
+        float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]) - cm[1];
+        float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]) - cm[2];
+        Q[0] += q0.x;
+        Q[1] += q0.y;
+        Q[2] += q0.z;
+        Q[3] += q0.w;
+        Q[4] += q1.x;
+        Q[5] += q1.y;
+        add_point_quad(Q, a.w, dx, dy, dz);
+      }
+      write_cell(mom, p, G, M, cm, Q);
+      cur = p;
+    }
+  }
+}
+
+// Opening radius of Eq. 1 for this theta: r_open = l/theta + delta, beside the
+// centre of mass (high part) that the walk's opening test reads.
+__global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ counts, const float4 *__restrict__ mom,
+                                                float inv_theta, float4 *mac, uint32_t *queue) {
+  const int C = counts[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *queue = 0;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    float4 a = mom[4 * (size_t)c];
+    float delta = mom[4 * (size_t)c + 1].w;
+    float l = mom[4 * (size_t)c + 3].z;
+    mac[c] = make_float4(a.x, a.y, a.z, fmaf(l, inv_theta, delta));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
+  const int nb = c.num_sms * 8;
+  if (c.n_sys > 1)
+    k_moments<true><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level, c.c_pbeg,
+                                          c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr, c.part_hi, c.part_lo,
+                                          c.c_mom);
+  else
+    k_moments<false><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level, c.c_pbeg,
+                                           c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr, c.part_hi,
+                                           c.part_lo, c.c_mom);
+  c.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s) {
+  float inv = (theta > 0.f) ? 1.0f / theta : INFINITY;
+  k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue);
+  c.launches++;
+  return cudaGetLastError();
+}
+
+}  // namespace bh

@@ -1,0 +1,269 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Integer work (keys, sort permutation, cells, links, groups) is compared bit
+for bit; moments and forces within the tolerances of tests/_parity.py.
+Inputs are seeded and synthetic, sized so the oracle finishes in seconds
+while spanning several sort tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import ics
+import oracle
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a, dtype=None):
+    import torch
+
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _run(bh, pos, mass, theta, eps, n_leaf=16, n_crit=64, offsets=None, **kw):
+    import torch
+
+    n = len(pos)
+    nsys = 1 if offsets is None else len(offsets) - 1
+    tc = bh.TreeCode(max(n, 1), max(nsys, 1), n_leaf=n_leaf, n_crit=n_crit, **kw)
+    p, m = _dev(pos), _dev(mass)
+    tc.build(p, m, offsets=offsets)
+    acc = torch.full((n, 3), float("nan"), dtype=torch.float32, device="cuda")
+    pot = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    tc.compute_forces(theta, eps, acc, pot)
+    tc.check()
+    return tc, acc.cpu().numpy(), pot.cpu().numpy()
+
+
+def _full_parity(bh, pos, mass, theta, eps, n_leaf=16, n_crit=64, offsets=None, **kw):
+    tc, acc, pot = _run(bh, pos, mass, theta, eps, n_leaf, n_crit, offsets, **kw)
+    acc_o, pot_o, t, st_o = oracle.tree_forces(pos, mass, theta, eps, n_leaf, n_crit, offsets)
+    P.compare_tree(tc.tree(), t)
+    if t.C:
+        P.compare_moments(tc.moments(), t)
+    rep = P.compare_forces(acc, pot, acc_o, pot_o, t, st_o, tc.group_stats())
+    return tc, t, rep
+
+
+# ------------------------------------------------------------- App. A scan
+def test_scan_worked_example(cuda_lib):
+    import torch
+
+    tc = cuda_lib.TreeCode(1 << 16)
+    x = torch.tensor([3, 1, 7, 0, 4, 1, 6, 3], dtype=torch.int32, device="cuda")
+    ex, total = tc.exclusive_scan(x)
+    inclusive = (ex + x).cpu().numpy().tolist()
+    assert inclusive == [3, 4, 11, 11, 15, 16, 22, 25]
+    assert total == 25
+
+
+@pytest.mark.parametrize("n", [1, 4095, 4096, 4097, 60001])
+def test_scan_random(cuda_lib, n):
+    import torch
+
+    tc = cuda_lib.TreeCode(1 << 16)
+    x = np.random.default_rng(n).integers(0, 50, n).astype(np.int32)
+    ex, total = tc.exclusive_scan(torch.from_numpy(x).cuda())
+    want = np.concatenate([[0], np.cumsum(x)[:-1]])
+    assert np.array_equal(ex.cpu().numpy(), want) and total == int(x.sum())
+
+
+# ----------------------------------------------------------- plain systems
+def test_plummer_16k_parity(cuda_lib):
+    pos, _, m = ics.plummer(16384, 1)
+    _, t, rep = _full_parity(cuda_lib, pos, m, 0.5, 0.01)
+    print("plummer 16384:", rep)
+    assert rep["flipped_groups"] <= max(2, t.G // 100)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.75])
+def test_plummer_ragged_theta(cuda_lib, theta):
+    pos, _, m = ics.plummer(10007, 17)
+    _full_parity(cuda_lib, pos, m, theta, 0.005)
+
+
+def test_eps_zero(cuda_lib):
+    pos, _, m = ics.plummer(5000, 3)
+    _full_parity(cuda_lib, pos, m, 0.5, 0.0)
+
+
+@pytest.mark.parametrize("n_leaf,n_crit", [(1, 1), (4, 8), (8, 32), (16, 16), (32, 64), (64, 64)])
+def test_parameters(cuda_lib, n_leaf, n_crit):
+    pos, _, m = ics.plummer(3000, 9)
+    _full_parity(cuda_lib, pos, m, 0.6, 0.01, n_leaf=n_leaf, n_crit=n_crit)
+
+
+def test_theta_zero_is_direct(cuda_lib):
+    pos, _, m = ics.plummer(2000, 12)
+    _, acc, pot = _run(cuda_lib, pos, m, 0.0, 0.01, n_leaf=8, n_crit=32)
+    ad, pd = oracle.direct(pos, m, 0.01)
+    err = np.linalg.norm(acc - ad, axis=1) / np.linalg.norm(ad, axis=1)
+    assert err.max() < 1e-5
+    assert np.max(np.abs(pot - pd) / np.abs(pd)) < 1e-5
+
+
+def test_edge_cases(cuda_lib):
+    rng = np.random.default_rng(4)
+    cases = [
+        np.array([[1.0, 2.0, 3.0]]),
+        np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]]),
+        rng.uniform(size=(17, 3)),
+        rng.uniform(size=(16, 3)),  # root is a leaf
+        np.concatenate([rng.uniform(size=(60, 3)), np.zeros((30, 3)) + 0.5]),  # coincident bodies
+        np.concatenate([rng.uniform(size=(200, 3)) * 1e-3, [[1e3, 1e3, 1e3]]]),  # one far away
+        rng.uniform(size=(300, 3)) * np.array([1e-7, 1.0, 1.0]),  # flat
+        np.zeros((100, 3)) + 0.25,  # all coincident: depth-20 leaf, chunked groups
+    ]
+    for pos in cases:
+        m = rng.uniform(0.5, 1.5, len(pos)) / len(pos)
+        _full_parity(cuda_lib, pos, m, 0.5, 0.01, n_leaf=16, n_crit=32)
+
+
+def test_nonfinite_input_is_reported(cuda_lib):
+    import torch
+
+    pos, _, m = ics.plummer(1000, 2)
+    pos[17, 1] = np.nan
+    tc = cuda_lib.TreeCode(1000)
+    tc.build(_dev(pos), _dev(m))
+    assert tc.status() == 3  # BH_ERR_NONFINITE
+    pos[17, 1] = 0.0
+    tc.build(_dev(pos), _dev(m))
+    acc = torch.empty((1000, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty(1000, dtype=torch.float32, device="cuda")
+    tc.compute_forces(0.5, 0.01, acc, pot)
+    assert tc.status() == 0
+
+
+def test_stack_overflow_is_reported(cuda_lib):
+    import torch
+
+    pos, _, m = ics.plummer(4000, 5)
+    tc = cuda_lib.TreeCode(4000, stack_capacity=64)
+    tc.build(_dev(pos), _dev(m))
+    acc = torch.empty((4000, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty(4000, dtype=torch.float32, device="cuda")
+    tc.compute_forces(0.0, 0.01, acc, pot)  # theta = 0 opens everything: a wide frontier
+    assert tc.status() == 2  # BH_ERR_CAPACITY
+    assert tc.status() == 0  # the status word was cleared
+
+
+# ----------------------------------------------------------------- forest
+def test_forest_parity(cuda_lib):
+    pos, _, m, off = ics.ensemble(n_sys=40, seed=9, n_min=1, n_max=3000)
+    tc, t, _ = _full_parity(cuda_lib, pos, m, 0.5, 0.01, offsets=off)
+    # each system alone gives the same tables and forces (the forest shares nothing across systems)
+    for s in [0, 7, 39]:
+        b, e = off[s], off[s + 1]
+        ts, acc_s, pot_s = _run(cuda_lib, pos[b:e], m[b:e], 0.5, 0.01)
+        assert np.array_equal(ts.tree()["perm"], tc.tree()["perm"][b:e] - b)
+
+
+def test_forest_with_empty_systems(cuda_lib):
+    pos, _, m = ics.plummer(500, 4)
+    off = np.array([0, 0, 130, 130, 131, 500, 500])
+    _full_parity(cuda_lib, pos, m, 0.5, 0.01, offsets=off)
+
+
+# ---------------------------------------------------------------- host e2e
+def test_forces_host_equals_device(cuda_lib):
+    import torch
+
+    pos, _, m = ics.plummer(8192, 6)
+    tc, acc, pot = _run(cuda_lib, pos, m, 0.5, 0.01)
+    hp = torch.from_numpy(pos).pin_memory()
+    hm = torch.from_numpy(m).pin_memory()
+    ha = torch.empty((8192, 3), dtype=torch.float32).pin_memory()
+    hq = torch.empty(8192, dtype=torch.float32).pin_memory()
+    tc.forces_host(hp, hm, 0.5, 0.01, ha, hq)
+    assert np.array_equal(ha.numpy(), acc) and np.array_equal(hq.numpy(), pot)
+
+
+# ---------------------------------------------------------------- leapfrog
+def _state_run(bh, pos, vel, m, steps, dt, theta, eps, graph=False, offsets=None):
+    import torch
+
+    n = len(pos)
+    tc = bh.TreeCode(n, 1 if offsets is None else len(offsets) - 1)
+    tc.set_state(_dev(pos), _dev(vel), _dev(m), offsets=offsets)
+    for _ in range(steps):
+        tc.step(dt, theta, eps, graph=graph)
+    x = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    v = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+    a = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    p = torch.empty(n, dtype=torch.float32, device="cuda")
+    tc.get_state(x, v, a, p)
+    tc.check()
+    return tc, x.cpu().numpy(), v.cpu().numpy(), a.cpu().numpy(), p.cpu().numpy()
+
+
+def test_leapfrog_matches_oracle_steps(cuda_lib):
+    pos, vel, m = ics.plummer(3000, 31)
+    dt, theta, eps, steps = 1 / 64, 0.5, 0.01, 5
+    _, x, v, a, p = _state_run(cuda_lib, pos, vel, m, steps, dt, theta, eps)
+    # oracle: same predictor-corrector with its own FP64 tree forces
+    accel = lambda xx: oracle.tree_forces(xx, m, theta, eps)[:2]
+    ao, _ = accel(pos)
+    xo, vo = pos.copy(), vel.copy()
+    for _ in range(steps):
+        xo, vo, ao, po = oracle.leapfrog_step(xo, vo, ao, dt, accel)
+    assert np.max(np.abs(x - xo)) < 1e-8
+    assert np.max(np.abs(v - vo)) < 1e-6
+    assert np.max(np.linalg.norm(a - ao, axis=1) / np.linalg.norm(ao, axis=1)) < 1e-3
+
+
+def test_two_body_orbit_energy(cuda_lib):
+    m = np.array([0.25, 0.75])
+    pos = np.array([[-0.75, 0, 0], [0.25, 0, 0]])
+    vel = np.array([[0, -0.75, 0], [0, 0.25, 0]])
+    steps = 1000
+    tc, x, v, a, p = _state_run(cuda_lib, pos, vel, m, steps, 2 * np.pi / steps, 0.5, 0.0)
+    d = tc.diagnostics()
+    e0 = -m[0] * m[1] / 2.0
+    assert abs((d["ekin"] + d["epot"]) / e0 - 1) < 1e-5
+    assert np.max(np.abs(x - pos)) < 1e-3
+
+
+def test_graph_step_equals_eager(cuda_lib):
+    pos, vel, m = ics.plummer(20000, 32)
+    _, x1, v1, a1, _ = _state_run(cuda_lib, pos, vel, m, 4, 1 / 64, 0.5, 0.01, graph=False)
+    _, x2, v2, a2, _ = _state_run(cuda_lib, pos, vel, m, 4, 1 / 64, 0.5, 0.01, graph=True)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(a1, a2)
+
+
+def test_forest_step_equals_systems(cuda_lib):
+    pos, vel, m, off = ics.ensemble(n_sys=6, seed=7, n_min=500, n_max=4000)
+    _, xf, vf, _, _ = _state_run(cuda_lib, pos, vel, m, 3, 1 / 64, 0.5, 0.01, offsets=off)
+    for s in range(6):
+        b, e = off[s], off[s + 1]
+        _, xs, vs, _, _ = _state_run(cuda_lib, pos[b:e], vel[b:e], m[b:e], 3, 1 / 64, 0.5, 0.01)
+        assert np.allclose(xf[b:e], xs, rtol=0, atol=1e-12)
+        assert np.allclose(vf[b:e], vs, rtol=0, atol=1e-9)
+
+
+# ------------------------------------------------- full-size (1M) sampled
+def test_plummer_1m_sampled(cuda_lib):
+    """The benchmark's workload: integer tables bit-exact, forces on every
+    400th group against the oracle walking the same groups."""
+    pos, _, m = ics.plummer(1 << 20, 2)
+    tc, acc, pot = _run(cuda_lib, pos, m, 0.5, 0.005)
+    t = oracle.build_tree(pos, m)
+    P.compare_tree(tc.tree(), t)
+    groups = np.arange(0, t.G, 400)
+    acc_s, pot_s, st = oracle.walk(t, 0.5, 0.005, groups)
+    gst = tc.group_stats()
+    sub = {k: v[groups] for k, v in gst.items()}
+    same = (sub["nc"] == st["nc"]) & (sub["np"] == st["np"]) & (sub["csum"] == st["csum"]) & (
+        sub["psum"] == st["psum"])
+    assert np.all(st["margin"][~same] < P.MARGIN)
+    bodies = np.concatenate([np.arange(t.gbeg[g], t.gend[g]) for g in groups[same]])
+    inp = t.perm[bodies]
+    an = np.linalg.norm(acc_s[bodies], axis=1)
+    scale = np.maximum(an, P.KAPPA * st["amag"][bodies])
+    rel = np.linalg.norm(acc[inp] - acc_s[bodies], axis=1) / scale
+    prel = np.abs(pot[inp] - pot_s[bodies]) / np.abs(pot_s[bodies])
+    assert rel.max() <= P.TOL and prel.max() <= P.TOL
