@@ -195,6 +195,30 @@ int bh_walk_time(bh_ctx *ctx, float *ms);
 int bh_prim_exclusive_scan(bh_ctx *ctx, const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_host,
                            void *stream);
 
+/* Exclusive prefix sum (the same operation as bh_prim_exclusive_scan) for
+ * callers that cannot allocate device memory.  The paper has no counterpart:
+ * this entry point exists for callers that are handed device buffers by an
+ * application which owns all GPU memory, or that run under a device-memory
+ * budget set by someone else, and so can neither allocate nor bind a
+ * workspace.  It needs no context.
+ *
+ * in_dev[n], out_dev[n] (uint32, device): out_dev[i] = in_dev[0] + ... +
+ * in_dev[i-1].  total_dev (device, may be NULL): receives the sum of all n
+ * values as uint64.  Stream-ordered, no host synchronisation.
+ *
+ * Its only scratch is a fixed array compiled into the library (64 KiB +
+ * 8 bytes), held by every GPU that loads the library until the process
+ * exits.  It allocates nothing, so n is limited to BH_NOALLOC_SCAN_MAX_N:
+ * larger n returns BH_ERR_CAPACITY before anything is launched.  The first
+ * call on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the one array (no call relies on what an earlier call left in it),
+ * so calls that overlap on the GPU -- on different streams, or from
+ * different host threads -- race: serialise them. */
+#define BH_NOALLOC_SCAN_MAX_N (1ll << 26)
+int bh_exclusive_scan_noalloc(const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_dev,
+                              void *stream);
+
 /* A FP32 fused-multiply-add throughput probe: runs `iters` dependent FMA
  * chains on every resident thread and returns the achieved FP32 FLOP/s
  * (2 per FMA) in *flops.  Used to state the walk's FP32 roofline. */

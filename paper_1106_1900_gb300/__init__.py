@@ -134,7 +134,11 @@ _SIG = {
     "bh_prim_exclusive_scan": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                ctypes.c_void_p, ctypes.c_void_p],
     "bh_fp32_peak_probe": [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
+    "bh_exclusive_scan_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p],
 }
+
+NOALLOC_SCAN_MAX_N = 1 << 26
 
 
 def exported_symbols() -> list[str]:
@@ -194,6 +198,20 @@ def fp32_peak(device: int = 0, iters: int = 4096, stream=None) -> float:
     out = ctypes.c_double(0)
     _check(load().bh_fp32_peak_probe(device, iters, ctypes.byref(out), _stream(stream)), "bh_fp32_peak_probe")
     return out.value
+
+
+def exclusive_scan_noalloc(x, out=None, total=None, stream=None):
+    """Exclusive prefix sum of a uint32/int32 CUDA tensor through
+    ``bh_exclusive_scan_noalloc`` (no context, no workspace; the library
+    allocates nothing).  ``total``, if given, is a 1-element int64 CUDA tensor
+    that receives the sum."""
+    import torch
+
+    if out is None:
+        out = torch.empty_like(x)
+    _check(load().bh_exclusive_scan_noalloc(_ptr(x), _ptr(out), x.numel(), _ptr(total), _stream(stream)),
+           "bh_exclusive_scan_noalloc")
+    return out
 
 
 class TreeCode:

@@ -119,6 +119,9 @@ cudaError_t launch_move(Ctx &c, const double *pos, const double *mass, cudaStrea
 cudaError_t launch_move_state(Ctx &c, cudaStream_t s);  // gather state cur -> other, fills part_hi/lo
 cudaError_t launch_cells(Ctx &c, cudaStream_t s);
 cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *blocks, uint64_t *total,
+                                cudaStream_t s);
+int64_t scan_blocks_for(int64_t n);
 // k_moments.cu
 cudaError_t launch_moments(Ctx &c, cudaStream_t s);
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s);

@@ -806,6 +806,20 @@ cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n
   return cudaGetLastError();
 }
 
+// The same three scan kernels with caller-chosen scratch: `blocks` holds
+// scan_blocks_for(n) block sums, `total` receives the sum of all n values.
+cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *blocks, uint64_t *total,
+                                cudaStream_t s) {
+  int nb = cdiv(n, kScanTile);
+  if (nb == 0) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);
+  k_scan_up<<<nb, kBlock, 0, s>>>(in, n, blocks);
+  k_scan_mid<<<1, 1024, 0, s>>>(blocks, nb, total);
+  k_scan_down<<<nb, kBlock, 0, s>>>(in, n, blocks, out);
+  return cudaGetLastError();
+}
+
+int64_t scan_blocks_for(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
 cudaError_t launch_cells(Ctx &c, cudaStream_t s) {
   const int n = (int)c.n;
   const int W = cdiv(n, 32);
