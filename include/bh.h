@@ -59,7 +59,7 @@ typedef struct bh_params {
     int32_t walk_variant;   /* 0: FP32 in group-relative coordinates with compensated
                                accumulation across list tiles (default);
                                1: naive FP32 (absolute coordinates, plain sums) */
-    int32_t walk_warps;     /* warps per walk block, 1..16, default 4 */
+    int32_t walk_warps;     /* warps per walk block, 1..4, default 4 */
     int32_t walk_blocks_per_sm; /* persistent walk grid = SMs x this; 0 = occupancy */
     int32_t reserved[2];    /* must be 0 */
 } bh_params;

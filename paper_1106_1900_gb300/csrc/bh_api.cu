@@ -35,7 +35,7 @@ int validate_params(const bh_params *p) {
   if (p->n_crit < p->n_leaf || p->n_crit > 64) return BH_ERR_INVALID_ARG;
   if (p->stack_capacity < 64) return BH_ERR_INVALID_ARG;
   if (p->walk_variant < 0 || p->walk_variant > 1) return BH_ERR_INVALID_ARG;
-  if (p->walk_warps < 1 || p->walk_warps > 16) return BH_ERR_INVALID_ARG;
+  if (p->walk_warps < 1 || p->walk_warps > 4) return BH_ERR_INVALID_ARG;  // the walk is compiled for <= 128 threads
   if (p->walk_blocks_per_sm < 0 || p->walk_blocks_per_sm > 64) return BH_ERR_INVALID_ARG;
   return BH_OK;
 }

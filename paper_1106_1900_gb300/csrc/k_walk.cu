@@ -4,11 +4,11 @@
 // a global counter (a persistent kernel), so the walk has no block-wide
 // barrier at all.  Per group:
 //
-//  * every lane holds two target slots.  A group of more than 32 bodies maps
-//    one body per slot; 17..32 bodies put each body in both slots of its lane
-//    and split the sources between them; <= 16 bodies use four slots (two
-//    lanes) per body and split the sources four ways -- the paper's
-//    "several threads per particle" for small groups, with a final reduction.
+//  * every lane holds two target slots, 64 per warp.  A group of n bodies
+//    gets k = floor(64/n) slots per body (one for n > 32): slot s holds body
+//    s mod n and takes every k-th source starting at s div n, and the slots of
+//    a body are summed when the group ends -- the paper's "several threads
+//    per particle" for small groups, generalised so that few slots idle.
 //  * the current level of the walk is read 32 cells at a time from a
 //    per-warp stack in global memory; each lane applies Eq. 1 to one cell
 //    (d^2 > (l/theta + delta)^2, d = distance from the cell's centre of mass
@@ -20,15 +20,18 @@
 //    every lane sums the 32 interactions on its slots; the remainders are
 //    flushed when the walk ends.
 //
-// Precision (variant 0): all coordinates are taken relative to the group
-// centre c (a float: the first body's position), sources as
-// (x_hi - c) + x_lo from their two-float form, so close pairs keep their
-// relative accuracy; each 32-entry tile is summed in FP32 and tiles are
-// added into a (hi, lo) pair by TwoSum.  Variant 1 is the naive form:
-// absolute FP32 coordinates and plain sums.  A body is never paired with
-// itself: particle tiles that hold bodies of the walking group (a ballot tells)
-// run a loop that skips equal indices; all other tiles run the plain loop.
-// With eps = 0 zero distances are skipped as well.
+// Precision (variant 0): coordinates are offsets from the group centre c (a
+// float: the first body's position), each kept as two floats -- the rounded
+// offset and its exact residual -- built from the two-float body positions.
+// Particle-particle terms difference both parts, so a close pair stays
+// accurate however far from c it lies; particle-cell terms use the rounded
+// part (accepted cells lie at least l/theta from the group's box).  Partial
+// sums (about 32 interactions per slot) are folded into a (hi, lo) pair by
+// TwoSum.  Variant 1 is the naive form: absolute FP32 coordinates and plain
+// sums.  A body is never paired with itself: particle tiles that hold bodies
+// of the walking group (a ballot tells) run a loop that skips equal indices;
+// all other tiles run the plain loop.  With eps = 0 zero distances are
+// skipped as well.
 #include <cuda_runtime.h>
 
 #include "bh_internal.cuh"
@@ -39,9 +42,14 @@ namespace {
 struct WarpSmem {
   int clist[64];
   int plist[64];
-  float4 sc[36][3];  // staged cells: (dx, dy, dz, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0)
-  float4 sp[36];     // staged bodies: (dx, dy, dz, m)
-  int pidx[36];      // their sorted indices (read only for tiles holding the group's own bodies)
+  // staged cells: (dx, dy, dz, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0); entries >= 32 stay null
+  float4 sc[64][3];
+  // staged bodies: (S_hi, m), (S_lo, 0) -- offsets from the group centre as two floats;
+  // reused for the per-slot partial sums when a group ends (then re-nulled)
+  float4 sp[64][2];
+  int pidx[64];  // their sorted indices (read only for tiles holding the group's own bodies)
+  float box[6];  // group bounding box (min xyz, max xyz), offsets from the centre
+  float ctr[3];  // group centre
 };
 
 struct WalkArgs {
@@ -72,6 +80,8 @@ struct WalkArgs {
 };
 
 constexpr float kFar = 1e18f;
+constexpr int kWalkThreads = 128;  // 4 warps per block
+constexpr int kWalkMinBlocks = 5;  // 20 resident warps per SM (96 registers)
 
 struct Acc {
   float x, y, z, p;
@@ -85,8 +95,16 @@ __device__ __forceinline__ void two_sum_into(float &hi, float &lo, float v) {
   lo += e;
 }
 
+// a - b rounded, and the exact rounding error of that subtraction (Knuth's TwoSum).
+__device__ __forceinline__ float two_diff(float a, float b, float &err) {
+  float s = a - b;
+  float bb = s - a;
+  err = (a - (s - bb)) - (b + bb);
+  return s;
+}
+
 template <int VAR>
-__device__ __forceinline__ void fold_tile(Acc &hi, Acc &lo, const Acc &t) {
+__device__ __forceinline__ void fold(Acc &hi, Acc &lo, Acc &t) {
   if (VAR == 0) {
     two_sum_into(hi.x, lo.x, t.x);
     two_sum_into(hi.y, lo.y, t.y);
@@ -98,23 +116,40 @@ __device__ __forceinline__ void fold_tile(Acc &hi, Acc &lo, const Acc &t) {
     hi.z += t.z;
     hi.p += t.p;
   }
+  t = Acc{0.f, 0.f, 0.f, 0.f};
 }
 
-// Softened particle-particle interaction of source s = (dx, dy, dz, m) on a
-// target at (tx, ty, tz): 20 flops by the convention FMA = 2, rsqrt = 1.
-// SELF: the tile holds bodies of the walking group, so the pair of a body
-// with itself (same index) is skipped; GUARD: eps = 0, zero distances skipped.
-template <bool GUARD, bool SELF = false>
-__device__ __forceinline__ void pp(Acc &a, float tx, float ty, float tz, const float4 s, float eps2,
+struct Target {
+  float hx, hy, hz;  // offset from the group centre, rounded
+  float lx, ly, lz;  // its residual (variant 0) so that hi + lo is the offset to ~2^-48
+};
+
+// Softened particle-particle interaction of a staged source (S_hi, m), S_lo on
+// a target: 20 flops by the convention FMA = 2, rsqrt = 1 (the two-float
+// difference d = (S_hi - T_hi) + (S_lo - T_lo) costs 6 more: its first term is
+// exact for close pairs, so a pair keeps its relative accuracy however far it
+// is from the group centre).  SELF: skip the pair of a body with itself (same
+// index); GUARD: eps = 0, zero distances skipped.
+template <int VAR, bool GUARD, bool SELF>
+__device__ __forceinline__ void pp(Acc &a, const Target &t, const float4 sh, const float4 sl, float eps2,
                                    int me = 0, int other = 1) {
-  float dx = s.x - tx, dy = s.y - ty, dz = s.z - tz;
+  float dx, dy, dz;
+  if (VAR == 0) {
+    dx = (sh.x - t.hx) + (sl.x - t.lx);
+    dy = (sh.y - t.hy) + (sl.y - t.ly);
+    dz = (sh.z - t.hz) + (sl.z - t.lz);
+  } else {
+    dx = sh.x - t.hx;
+    dy = sh.y - t.hy;
+    dz = sh.z - t.hz;
+  }
   float r2 = fmaf(dx, dx, eps2);
   r2 = fmaf(dy, dy, r2);
   r2 = fmaf(dz, dz, r2);
   float ri = rsqrtf(r2);
   if (GUARD) ri = (r2 > 0.f) ? ri : 0.f;
   if (SELF) ri = (me == other) ? 0.f : ri;
-  float mr = s.w * ri;
+  float mr = sh.w * ri;
   float mr3 = mr * ri * ri;
   a.p -= mr;
   a.x = fmaf(mr3, dx, a.x);
@@ -124,9 +159,10 @@ __device__ __forceinline__ void pp(Acc &a, float tx, float ty, float tz, const f
 
 // Softened particle-cell interaction, monopole + quadrupole, with d = com -
 // target: a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7, phi = -M/s - (d.Q.d)/(2 s^5).
-__device__ __forceinline__ void pc(Acc &a, float tx, float ty, float tz, const float4 c0, const float4 q0,
-                                   const float4 q1, float eps2) {
-  float dx = c0.x - tx, dy = c0.y - ty, dz = c0.z - tz;
+// 54 flops by the convention above.
+__device__ __forceinline__ void pc(Acc &a, const Target &t, const float4 c0, const float4 q0, const float4 q1,
+                                   float eps2) {
+  float dx = c0.x - t.hx, dy = c0.y - t.hy, dz = c0.z - t.hz;
   float r2 = fmaf(dx, dx, eps2);
   r2 = fmaf(dy, dy, r2);
   r2 = fmaf(dz, dz, r2);
@@ -147,8 +183,28 @@ __device__ __forceinline__ void pc(Acc &a, float tx, float ty, float tz, const f
   a.z = fmaf(-ri5, qz, fmaf(coef, dz, a.z));
 }
 
+template <int VAR>
+__device__ __forceinline__ Target make_target(float4 h, float4 l, float cx, float cy, float cz) {
+  Target t;
+  if (VAR == 0) {
+    float ex, ey, ez;
+    t.hx = two_diff(h.x, cx, ex);
+    t.hy = two_diff(h.y, cy, ey);
+    t.hz = two_diff(h.z, cz, ez);
+    t.lx = ex + l.x;
+    t.ly = ey + l.y;
+    t.lz = ez + l.z;
+  } else {
+    t.hx = h.x;
+    t.hy = h.y;
+    t.hz = h.z;
+    t.lx = t.ly = t.lz = 0.f;
+  }
+  return t;
+}
+
 template <int VAR, bool GUARD, int MODE>
-__global__ void k_walk(WalkArgs A) {
+__global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks) k_walk(WalkArgs A) {
   extern __shared__ WarpSmem s_warp[];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -158,13 +214,15 @@ __global__ void k_walk(WalkArgs A) {
   int *nxt = cur + A.cap;
   const unsigned lt = lanemask_lt();
   const float eps2 = A.eps2;
-  if (lane < 4) {
-    S.sc[32 + lane][0] = make_float4(kFar, kFar, kFar, 0.f);
-    S.sc[32 + lane][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    S.sc[32 + lane][2] = make_float4(0.f, 0.f, 0.f, 0.f);
-    S.sp[32 + lane] = make_float4(kFar, kFar, kFar, 0.f);
-    S.pidx[32 + lane] = -1;
-  }
+  const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // entries 32..63 of the staging arrays are permanent nulls (zero mass, far away)
+  S.sc[32 + lane][0] = null_src;
+  S.sc[32 + lane][1] = zero4;
+  S.sc[32 + lane][2] = zero4;
+  S.sp[32 + lane][0] = null_src;
+  S.sp[32 + lane][1] = zero4;
+  S.pidx[32 + lane] = -1;
   __syncwarp();
   const int G = A.counts[1];
 
@@ -176,21 +234,27 @@ __global__ void k_walk(WalkArgs A) {
     const int gb = A.g_beg[g];
     const int n = A.g_beg[g + 1] - gb;
     const int root = A.sys_root[A.g_sys[g]];
-    const int tpp = (n <= 16) ? 4 : ((n <= 32) ? 2 : 1);
-    int p0, p1, ph0;
-    if (tpp == 1) {
-      p0 = lane;
-      p1 = lane + 32;
-      ph0 = 0;
-    } else if (tpp == 2) {
-      p0 = p1 = lane;
-      ph0 = 0;
+    // slots: a group of n bodies gets k = floor(64/n) slots per body (one for
+    // n > 32); slot s holds body s % n and takes the sources j = s / n (mod k)
+    const int k = (n > 32) ? 1 : min(64 / n, 32);
+    int b0, b1, ph0, ph1;
+    bool v0, v1;
+    if (k == 1) {
+      b0 = lane;
+      b1 = lane + 32;
+      ph0 = ph1 = 0;
+      v0 = b0 < n;
+      v1 = b1 < n;
     } else {
-      p0 = p1 = lane & 15;
-      ph0 = lane >> 4;
+      const int ns = n * k;
+      v0 = lane < ns;
+      v1 = lane + 32 < ns;
+      b0 = lane % n;
+      b1 = (lane + 32) % n;
+      ph0 = v0 ? lane / n : 0;
+      ph1 = v1 ? (lane + 32) / n : 0;
     }
-    const bool v0 = p0 < n, v1 = p1 < n;
-    // group centre and targets (same arithmetic as the staged sources)
+    // group centre (a float: the first body) and the slots' targets
     float cx = 0.f, cy = 0.f, cz = 0.f;
     if (VAR == 0) {
       float4 c = A.part_hi[gb];
@@ -198,37 +262,16 @@ __global__ void k_walk(WalkArgs A) {
       cy = c.y;
       cz = c.z;
     }
-    float t0x, t0y, t0z, t1x, t1y, t1z;
-    {
-      float4 h = A.part_hi[gb + min(p0, n - 1)], l = A.part_lo[gb + min(p0, n - 1)];
-      if (VAR == 0) {
-        t0x = (h.x - cx) + l.x;
-        t0y = (h.y - cy) + l.y;
-        t0z = (h.z - cz) + l.z;
-      } else {
-        t0x = h.x;
-        t0y = h.y;
-        t0z = h.z;
-      }
-      h = A.part_hi[gb + min(p1, n - 1)];
-      l = A.part_lo[gb + min(p1, n - 1)];
-      if (VAR == 0) {
-        t1x = (h.x - cx) + l.x;
-        t1y = (h.y - cy) + l.y;
-        t1z = (h.z - cz) + l.z;
-      } else {
-        t1x = h.x;
-        t1y = h.y;
-        t1z = h.z;
-      }
-    }
+    const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
+    const Target T0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
+    const Target T1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
     // tight bounding box of the group's bodies
-    float bminx = fminf(v0 ? t0x : INFINITY, v1 ? t1x : INFINITY);
-    float bminy = fminf(v0 ? t0y : INFINITY, v1 ? t1y : INFINITY);
-    float bminz = fminf(v0 ? t0z : INFINITY, v1 ? t1z : INFINITY);
-    float bmaxx = fmaxf(v0 ? t0x : -INFINITY, v1 ? t1x : -INFINITY);
-    float bmaxy = fmaxf(v0 ? t0y : -INFINITY, v1 ? t1y : -INFINITY);
-    float bmaxz = fmaxf(v0 ? t0z : -INFINITY, v1 ? t1z : -INFINITY);
+    float bminx = fminf(v0 ? T0.hx : INFINITY, v1 ? T1.hx : INFINITY);
+    float bminy = fminf(v0 ? T0.hy : INFINITY, v1 ? T1.hy : INFINITY);
+    float bminz = fminf(v0 ? T0.hz : INFINITY, v1 ? T1.hz : INFINITY);
+    float bmaxx = fmaxf(v0 ? T0.hx : -INFINITY, v1 ? T1.hx : -INFINITY);
+    float bmaxy = fmaxf(v0 ? T0.hy : -INFINITY, v1 ? T1.hy : -INFINITY);
+    float bmaxz = fmaxf(v0 ? T0.hz : -INFINITY, v1 ? T1.hz : -INFINITY);
     for (int o = 16; o > 0; o >>= 1) {
       bminx = fminf(bminx, __shfl_xor_sync(kFull, bminx, o));
       bminy = fminf(bminy, __shfl_xor_sync(kFull, bminy, o));
@@ -237,9 +280,32 @@ __global__ void k_walk(WalkArgs A) {
       bmaxy = fmaxf(bmaxy, __shfl_xor_sync(kFull, bmaxy, o));
       bmaxz = fmaxf(bmaxz, __shfl_xor_sync(kFull, bmaxz, o));
     }
+    if (lane == 0) {
+      S.box[0] = bminx;
+      S.box[1] = bminy;
+      S.box[2] = bminz;
+      S.box[3] = bmaxx;
+      S.box[4] = bmaxy;
+      S.box[5] = bmaxz;
+      S.ctr[0] = cx;
+      S.ctr[1] = cy;
+      S.ctr[2] = cz;
+    }
+    __syncwarp();
     Acc h0 = {0, 0, 0, 0}, l0 = {0, 0, 0, 0}, h1 = {0, 0, 0, 0}, l1 = {0, 0, 0, 0};
+    Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};  // partial sums since the last fold
+    int since = 0;                              // interactions per slot since the last fold
     int cn = 0, pn = 0, ncell = 0, npart = 0;
     unsigned long long csum = 0, psum = 0;
+
+    auto after_tile = [&](int cnt) {
+      since += (cnt + k - 1) / k;
+      if (since >= 32) {
+        fold<VAR>(h0, l0, t0);
+        fold<VAR>(h1, l1, t1);
+        since = 0;
+      }
+    };
 
     // ---- evaluate the first `cnt` entries of the cell list
     auto eval_cells = [&](int cnt) {
@@ -249,9 +315,9 @@ __global__ void k_walk(WalkArgs A) {
         float4 q0 = A.mom[4 * (size_t)cc + 2], q1 = A.mom[4 * (size_t)cc + 3];
         float dx, dy, dz;
         if (VAR == 0) {
-          dx = (a.x - cx) + b.x;
-          dy = (a.y - cy) + b.y;
-          dz = (a.z - cz) + b.z;
+          dx = (a.x - S.ctr[0]) + b.x;
+          dy = (a.y - S.ctr[1]) + b.y;
+          dz = (a.z - S.ctr[2]) + b.z;
         } else {
           dx = a.x;
           dy = a.y;
@@ -261,35 +327,26 @@ __global__ void k_walk(WalkArgs A) {
         S.sc[lane][1] = q0;
         S.sc[lane][2] = make_float4(q1.x, q1.y, 0.f, 0.f);
       } else {
-        S.sc[lane][0] = make_float4(kFar, kFar, kFar, 0.f);
-        S.sc[lane][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        S.sc[lane][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.sc[lane][0] = null_src;
+        S.sc[lane][1] = zero4;
+        S.sc[lane][2] = zero4;
       }
       __syncwarp();
-      Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};
-      if (tpp == 1) {
-#pragma unroll 2
+      if (k == 1) {
+#pragma unroll 1
         for (int j = 0; j < cnt; ++j) {
           const float4 c0 = S.sc[j][0], q0 = S.sc[j][1], q1 = S.sc[j][2];
-          pc(t0, t0x, t0y, t0z, c0, q0, q1, eps2);
-          pc(t1, t1x, t1y, t1z, c0, q0, q1, eps2);
-        }
-      } else if (tpp == 2) {
-#pragma unroll 2
-        for (int j = 0; j < cnt; j += 2) {
-          pc(t0, t0x, t0y, t0z, S.sc[j][0], S.sc[j][1], S.sc[j][2], eps2);
-          pc(t1, t1x, t1y, t1z, S.sc[j + 1][0], S.sc[j + 1][1], S.sc[j + 1][2], eps2);
+          pc(t0, T0, c0, q0, q1, eps2);
+          pc(t1, T1, c0, q0, q1, eps2);
         }
       } else {
-#pragma unroll 2
-        for (int j = 0; j < cnt; j += 4) {
-          const int s0 = j + ph0, s1 = j + ph0 + 2;
-          pc(t0, t0x, t0y, t0z, S.sc[s0][0], S.sc[s0][1], S.sc[s0][2], eps2);
-          pc(t1, t1x, t1y, t1z, S.sc[s1][0], S.sc[s1][1], S.sc[s1][2], eps2);
+#pragma unroll 1
+        for (int j = 0; j < cnt; j += k) {
+          pc(t0, T0, S.sc[j + ph0][0], S.sc[j + ph0][1], S.sc[j + ph0][2], eps2);
+          pc(t1, T1, S.sc[j + ph1][0], S.sc[j + ph1][1], S.sc[j + ph1][2], eps2);
         }
       }
-      fold_tile<VAR>(h0, l0, t0);
-      fold_tile<VAR>(h1, l1, t1);
+      after_tile(cnt);
       __syncwarp();
     };
 
@@ -299,50 +356,39 @@ __global__ void k_walk(WalkArgs A) {
       if (lane < cnt) {
         int b = S.plist[lane];
         member = (unsigned)(b - gb) < (unsigned)n;
-        float4 h = A.part_hi[b], l = A.part_lo[b];
-        if (VAR == 0)
-          S.sp[lane] = make_float4((h.x - cx) + l.x, (h.y - cy) + l.y, (h.z - cz) + l.z, h.w);
-        else
-          S.sp[lane] = h;
+        const Target s = make_target<VAR>(A.part_hi[b], A.part_lo[b], S.ctr[0], S.ctr[1], S.ctr[2]);
+        S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, A.part_hi[b].w);
+        S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
         S.pidx[lane] = b;
       } else {
-        S.sp[lane] = make_float4(kFar, kFar, kFar, 0.f);
+        S.sp[lane][0] = null_src;
+        S.sp[lane][1] = zero4;
         S.pidx[lane] = -1;
       }
       const bool self_tile = __any_sync(kFull, member);
       __syncwarp();
-      Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};
       if (self_tile) {
         // a tile with the group's own bodies: skip each body's pair with itself by index
-        const int me0 = gb + p0, me1 = gb + p1;
-        const int st = (tpp == 1) ? 1 : tpp;
-        const int o0 = (tpp == 1) ? 0 : ph0, o1 = (tpp == 1) ? 0 : ((tpp == 2) ? 1 : ph0 + 2);
-        for (int j = 0; j < cnt; j += st) {
-          pp<GUARD, true>(t0, t0x, t0y, t0z, S.sp[j + o0], eps2, me0, S.pidx[j + o0]);
-          pp<GUARD, true>(t1, t1x, t1y, t1z, S.sp[j + o1], eps2, me1, S.pidx[j + o1]);
+        const int me0 = gb + b0, me1 = gb + b1;
+        for (int j = 0; j < cnt; j += k) {
+          pp<VAR, GUARD, true>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2, me0, S.pidx[j + ph0]);
+          pp<VAR, GUARD, true>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2, me1, S.pidx[j + ph1]);
         }
-      } else if (tpp == 1) {
-#pragma unroll 4
+      } else if (k == 1) {
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
-          const float4 s = S.sp[j];
-          pp<GUARD>(t0, t0x, t0y, t0z, s, eps2);
-          pp<GUARD>(t1, t1x, t1y, t1z, s, eps2);
-        }
-      } else if (tpp == 2) {
-#pragma unroll 4
-        for (int j = 0; j < cnt; j += 2) {
-          pp<GUARD>(t0, t0x, t0y, t0z, S.sp[j], eps2);
-          pp<GUARD>(t1, t1x, t1y, t1z, S.sp[j + 1], eps2);
+          const float4 sh = S.sp[j][0], sl = S.sp[j][1];
+          pp<VAR, GUARD, false>(t0, T0, sh, sl, eps2);
+          pp<VAR, GUARD, false>(t1, T1, sh, sl, eps2);
         }
       } else {
-#pragma unroll 4
-        for (int j = 0; j < cnt; j += 4) {
-          pp<GUARD>(t0, t0x, t0y, t0z, S.sp[j + ph0], eps2);
-          pp<GUARD>(t1, t1x, t1y, t1z, S.sp[j + ph0 + 2], eps2);
+#pragma unroll 2
+        for (int j = 0; j < cnt; j += k) {
+          pp<VAR, GUARD, false>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2);
+          pp<VAR, GUARD, false>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2);
         }
       }
-      fold_tile<VAR>(h0, l0, t0);
-      fold_tile<VAR>(h1, l1, t1);
+      after_tile(cnt);
       __syncwarp();
     };
 
@@ -368,10 +414,10 @@ __global__ void k_walk(WalkArgs A) {
           m = A.mac[ci];
           lk = A.link[ci];
         }
-        float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
-        float ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
-        float ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy), 0.f);
-        float ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz), 0.f);
+        float rx = m.x - S.ctr[0], ry = m.y - S.ctr[1], rz = m.z - S.ctr[2];
+        float ex = fmaxf(fmaxf(S.box[0] - rx, rx - S.box[3]), 0.f);
+        float ey = fmaxf(fmaxf(S.box[1] - ry, ry - S.box[4]), 0.f);
+        float ez = fmaxf(fmaxf(S.box[2] - rz, rz - S.box[5]), 0.f);
         float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
         const bool accept = have && d2 > m.w * m.w;
         const bool open = have && !accept;
@@ -423,14 +469,14 @@ __global__ void k_walk(WalkArgs A) {
         const int pex = pin - np;
         for (int cb = 0; cb < ptot; cb += 32) {
           const int si = cb + lane;
-          int k = 0;
+          int kk = 0;
 #pragma unroll
           for (int step = 16; step > 0; step >>= 1) {
-            int v = __shfl_sync(kFull, pin, k + step - 1);
-            if (v <= si) k += step;
+            int v = __shfl_sync(kFull, pin, kk + step - 1);
+            if (v <= si) kk += step;
           }
-          const int of = __shfl_sync(kFull, lk.x, k);
-          const int oe = __shfl_sync(kFull, pex, k);
+          const int of = __shfl_sync(kFull, lk.x, kk);
+          const int oe = __shfl_sync(kFull, pex, kk);
           if (si < ptot) {
             const int body = of + (si - oe);
             S.plist[pn + lane] = body;
@@ -456,71 +502,51 @@ __global__ void k_walk(WalkArgs A) {
     }
     if (cn > 0) eval_cells(cn);
     if (pn > 0) eval_bodies(pn);
+    fold<VAR>(h0, l0, t0);
+    fold<VAR>(h1, l1, t1);
 
     // ---- combine the slots of each body and write
-    float ox, oy, oz, op;
-    if (tpp == 1) {
-      // slot 0: body p0, slot 1: body p1
-      if (v0 || v1) {
-        Acc r[2] = {{h0.x + l0.x, h0.y + l0.y, h0.z + l0.z, h0.p + l0.p},
-                    {h1.x + l1.x, h1.y + l1.y, h1.z + l1.z, h1.p + l1.p}};
-        const int pb[2] = {p0, p1};
-        const bool vv[2] = {v0, v1};
-        for (int s = 0; s < 2; ++s) {
-          if (!vv[s]) continue;
-          const int b = gb + pb[s];
-          if (MODE == kOutSorted) {
-            A.acc_sorted[b] = make_float4(r[s].x, r[s].y, r[s].z, r[s].p);
-          } else {
-            const size_t j = A.perm[b];
-            A.acc_out[3 * j] = r[s].x;
-            A.acc_out[3 * j + 1] = r[s].y;
-            A.acc_out[3 * j + 2] = r[s].z;
-            A.pot_out[j] = r[s].p;
-          }
-        }
+    auto write_body = [&](int b, float ox, float oy, float oz, float op) {
+      const int gi = gb + b;
+      if (MODE == kOutSorted) {
+        A.acc_sorted[gi] = make_float4(ox, oy, oz, op);
+      } else {
+        const size_t j = A.perm[gi];
+        A.acc_out[3 * j] = ox;
+        A.acc_out[3 * j + 1] = oy;
+        A.acc_out[3 * j + 2] = oz;
+        A.pot_out[j] = op;
       }
+    };
+    if (k == 1) {
+      if (v0) write_body(b0, h0.x + l0.x, h0.y + l0.y, h0.z + l0.z, h0.p + l0.p);
+      if (v1) write_body(b1, h1.x + l1.x, h1.y + l1.y, h1.z + l1.z, h1.p + l1.p);
     } else {
-      // both slots hold the same body: combine them (and, with four slots, the partner lane)
-      two_sum_into(h0.x, l0.x, h1.x);
-      two_sum_into(h0.y, l0.y, h1.y);
-      two_sum_into(h0.z, l0.z, h1.z);
-      two_sum_into(h0.p, l0.p, h1.p);
-      l0.x += l1.x;
-      l0.y += l1.y;
-      l0.z += l1.z;
-      l0.p += l1.p;
-      if (tpp == 4) {
-        float ux = __shfl_xor_sync(kFull, h0.x, 16), uy = __shfl_xor_sync(kFull, h0.y, 16);
-        float uz = __shfl_xor_sync(kFull, h0.z, 16), up = __shfl_xor_sync(kFull, h0.p, 16);
-        float wx = __shfl_xor_sync(kFull, l0.x, 16), wy = __shfl_xor_sync(kFull, l0.y, 16);
-        float wz = __shfl_xor_sync(kFull, l0.z, 16), wp = __shfl_xor_sync(kFull, l0.p, 16);
-        two_sum_into(h0.x, l0.x, ux);
-        two_sum_into(h0.y, l0.y, uy);
-        two_sum_into(h0.z, l0.z, uz);
-        two_sum_into(h0.p, l0.p, up);
-        l0.x += wx;
-        l0.y += wy;
-        l0.z += wz;
-        l0.p += wp;
-      }
-      ox = h0.x + l0.x;
-      oy = h0.y + l0.y;
-      oz = h0.z + l0.z;
-      op = h0.p + l0.p;
-      const bool writer = v0 && (tpp == 2 || lane < 16);
-      if (writer) {
-        const int b = gb + p0;
-        if (MODE == kOutSorted) {
-          A.acc_sorted[b] = make_float4(ox, oy, oz, op);
-        } else {
-          const size_t j = A.perm[b];
-          A.acc_out[3 * j] = ox;
-          A.acc_out[3 * j + 1] = oy;
-          A.acc_out[3 * j + 2] = oz;
-          A.pot_out[j] = op;
+      // slot s -> sp[s] = (hi), (lo); body b sums slots b, b + n, ..., b + n (k - 1)
+      S.sp[lane][0] = make_float4(h0.x, h0.y, h0.z, h0.p);
+      S.sp[lane][1] = make_float4(l0.x, l0.y, l0.z, l0.p);
+      S.sp[32 + lane][0] = make_float4(h1.x, h1.y, h1.z, h1.p);
+      S.sp[32 + lane][1] = make_float4(l1.x, l1.y, l1.z, l1.p);
+      __syncwarp();
+      if (lane < n) {
+        float4 H = S.sp[lane][0], L = S.sp[lane][1];
+        for (int q = 1; q < k; ++q) {
+          const float4 h = S.sp[lane + q * n][0], l = S.sp[lane + q * n][1];
+          two_sum_into(H.x, L.x, h.x);
+          two_sum_into(H.y, L.y, h.y);
+          two_sum_into(H.z, L.z, h.z);
+          two_sum_into(H.w, L.w, h.w);
+          L.x += l.x;
+          L.y += l.y;
+          L.z += l.z;
+          L.w += l.w;
         }
+        write_body(lane, H.x + L.x, H.y + L.y, H.z + L.z, H.w + L.w);
       }
+      __syncwarp();
+      S.sp[32 + lane][0] = null_src;
+      S.sp[32 + lane][1] = zero4;
+      __syncwarp();
     }
     // ---- group statistics
     for (int o = 16; o > 0; o >>= 1) {

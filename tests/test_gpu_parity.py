@@ -123,6 +123,17 @@ def test_edge_cases(cuda_lib):
         _full_parity(cuda_lib, pos, m, 0.5, 0.01, n_leaf=16, n_crit=32)
 
 
+@pytest.mark.parametrize("eps", [1e-4, 0.01])
+def test_close_pair_far_from_group_centre(cuda_lib, eps):
+    # a sparse group: its centre is the first body, 30 units away from a pair
+    # 1e-3 apart; the pair's force must keep FP32 relative accuracy
+    rng = np.random.default_rng(8)
+    pos = np.array([[0.0, 0.0, 0.0], [30.0, 0.2, -0.1], [30.001, 0.2003, -0.1004]])
+    pos = np.concatenate([pos, rng.uniform(-30, 30, size=(5, 3))])
+    m = rng.uniform(0.5, 1.5, len(pos))
+    _full_parity(cuda_lib, pos, m, 0.5, eps, n_leaf=16, n_crit=16)
+
+
 def test_nonfinite_input_is_reported(cuda_lib):
     import torch
 
