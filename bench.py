@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch kernel by kernel instead of the graph")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
+    ap.add_argument("--untuned", action="store_true", help="use the paper's N_leaf = 16, N_crit = 64")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
     return ap.parse_args()
 
 
@@ -191,6 +193,72 @@ def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
                       f"theta={theta}, eps={eps}"}
 
 
+def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
+    """512 independent Plummer clusters (sizes log-uniform in [1024, 65536],
+    scale radii U(0.5, 2)): one forest stepped as one CUDA graph per step
+    against one context per cluster, each stepping its own graph.  Both arms
+    compute identical forces (a forest's systems share nothing), so the
+    error is equal by construction; the final states are compared."""
+    import numpy as np
+    import torch
+
+    import ics
+
+    pos, vel, m, off = ics.ensemble(n_sys, 5)
+    N = len(pos)
+    P, V, M = (torch.from_numpy(a).to(dev) for a in (pos, vel, m))
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # batched: one forest, one graph per step
+    tf = bh.TreeCode(N, n_sys, device=dev.index)
+    tf.set_state(P, V, M, offsets=off)
+    for _ in range(warmup):
+        tf.step(DT, theta, eps, graph=True)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(steps):
+        tf.step(DT, theta, eps, graph=True)
+    b.record()
+    torch.cuda.synchronize()
+    tf.check()
+    t_batched = a.elapsed_time(b) * 1e-3
+    xf = torch.empty_like(P)
+    tf.get_state(xf)
+    tf.close()
+    # plain: one context and graph per system, launched one after another
+    ctxs = []
+    for s_ in range(n_sys):
+        lo, hi = int(off[s_]), int(off[s_ + 1])
+        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048)
+        tc.set_state(P[lo:hi], V[lo:hi], M[lo:hi])
+        ctxs.append((lo, hi, tc))
+    for _ in range(warmup):
+        for _, _, tc in ctxs:
+            tc.step(DT, theta, eps, graph=True)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(steps):
+        for _, _, tc in ctxs:
+            tc.step(DT, theta, eps, graph=True)
+    b.record()
+    torch.cuda.synchronize()
+    t_plain = a.elapsed_time(b) * 1e-3
+    maxdiff = 0.0
+    for lo, hi, tc in ctxs:
+        tc.check()
+        xs = torch.empty((hi - lo, 3), dtype=torch.float64, device=dev)
+        tc.get_state(xs)
+        maxdiff = max(maxdiff, float((xs - xf[lo:hi]).abs().max()))
+        tc.close()
+    return {"workload": f"{n_sys} Plummer clusters, N={N} (sizes log-uniform 1024..65536, seeds 5000+s), "
+                        f"theta={theta}, eps={eps}, dt=1/64",
+            "steps": steps, "batched_particles_per_s": N * steps / t_batched,
+            "plain_particles_per_s": N * steps / t_plain, "speedup": t_plain / t_batched,
+            "batched_ms_per_step": 1e3 * t_batched / steps, "plain_ms_per_step": 1e3 * t_plain / steps,
+            "max_state_difference": maxdiff}
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step builds the full tree and walks a sample of groups."""
     import numpy as np
@@ -260,7 +328,10 @@ def main():
     bh.load()
     n = args.n
     pos, vel, m = ics.plummer(n, SEED + rank)
-    tc = bh.TreeCode(n, device=local)
+    from paper_1106_1900_gb300 import autotune
+
+    tuned = None if args.untuned else autotune.tuned_params(n, args.theta)
+    tc = bh.TreeCode(n, device=local, **(tuned or {}))
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
@@ -320,7 +391,7 @@ def main():
         hm = torch.from_numpy(m).pin_memory()
         ha = torch.empty((n, 3), dtype=torch.float32).pin_memory()
         hq = torch.empty(n, dtype=torch.float32).pin_memory()
-        tc2 = bh.TreeCode(n, device=local)
+        tc2 = bh.TreeCode(n, device=local, **(tuned or {}))
         for _ in range(max(1, args.warmup)):
             tc2.forces_host(hp, hm, args.theta, EPS, ha, hq, stream=stream)
         if world > 1:
@@ -332,6 +403,9 @@ def main():
         e2e = {"value": bodies_all / e_s, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 8),
                "d2h_bytes_per_step": n * (12 + 4)}
         tc2.close()
+    ens = None
+    if not args.no_ensemble:
+        ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=3, warmup=2)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pos, m, args.theta, EPS)
@@ -347,6 +421,7 @@ def main():
                    "global_batch": n * world, "parallelism": f"independent system per GPU x{world}",
                    "l2": f"flushed between timed steps ({args.flush_mb} MB write)" if args.flush_mb else "not flushed",
                    "n_leaf": tc.params.n_leaf, "n_crit": tc.params.n_crit,
+                   "params": "autotuned (paper_1106_1900_gb300/tuned.json)" if tuned else "paper defaults",
                    "cells": cnt["cells"], "groups": cnt["groups"], "graph": not args.eager},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
@@ -360,6 +435,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "ensemble": ens,
         "wall_s_timed": wall1 - wall0,
     }
     print(json.dumps(out), flush=True)

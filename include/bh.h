@@ -195,6 +195,16 @@ int bh_walk_time(bh_ctx *ctx, float *ms);
 int bh_prim_exclusive_scan(bh_ctx *ctx, const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_host,
                            void *stream);
 
+/* Direct summation (§4.2.1 measures the tree's error against it; §3.3: theta
+ * -> 0 turns the tree-code into it): acceleration and potential on each listed
+ * target from every other body, softened like the particle-particle term.
+ * pos_dev [n][3] FP64, mass_dev [n] FP64, targets_dev [nt] int32 body
+ * indices; acc_dev [nt][3], pot_dev [nt] FP32 (pair differences from
+ * two-float positions, TwoSum-folded tile sums).  No context needed;
+ * stream-ordered.  O(nt * n) work: for subsamples and small systems. */
+int bh_direct_forces(const double *pos_dev, const double *mass_dev, int64_t n, const int32_t *targets_dev,
+                     int64_t nt, float eps, float *acc_dev, float *pot_dev, void *stream);
+
 /* Exclusive prefix sum (the same operation as bh_prim_exclusive_scan) for
  * callers that cannot allocate device memory.  The paper has no counterpart:
  * this entry point exists for callers that are handed device buffers by an

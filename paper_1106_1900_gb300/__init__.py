@@ -136,6 +136,8 @@ _SIG = {
     "bh_fp32_peak_probe": [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "bh_exclusive_scan_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_void_p],
+    "bh_direct_forces": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                         ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
 
 NOALLOC_SCAN_MAX_N = 1 << 26
@@ -198,6 +200,19 @@ def fp32_peak(device: int = 0, iters: int = 4096, stream=None) -> float:
     out = ctypes.c_double(0)
     _check(load().bh_fp32_peak_probe(device, iters, ctypes.byref(out), _stream(stream)), "bh_fp32_peak_probe")
     return out.value
+
+
+def direct_forces(pos, mass, targets, eps: float, stream=None):
+    """Direct-summation accelerations and potentials on ``targets`` (int32
+    CUDA tensor of body indices) from every other body: ``bh_direct_forces``."""
+    import torch
+
+    nt = targets.numel()
+    acc = torch.empty((nt, 3), dtype=torch.float32, device=pos.device)
+    pot = torch.empty(nt, dtype=torch.float32, device=pos.device)
+    _check(load().bh_direct_forces(_ptr(pos), _ptr(mass), pos.shape[0], _ptr(targets), nt, float(eps), _ptr(acc),
+                                   _ptr(pot), _stream(stream)), "bh_direct_forces")
+    return acc, pot
 
 
 def exclusive_scan_noalloc(x, out=None, total=None, stream=None):

@@ -139,6 +139,9 @@ cudaError_t launch_load_state(Ctx &c, const double *pos, const double *vel, cons
 cudaError_t launch_get_state(Ctx &c, double *pos, double *vel, float *acc, float *pot, cudaStream_t s);
 cudaError_t launch_diag(Ctx &c, cudaStream_t s);
 cudaError_t launch_fma_probe(int blocks, int threads, int iters, float *sink, cudaStream_t s);
+// k_direct.cu
+cudaError_t launch_direct(const double *pos, const double *mass, int n, const int32_t *targets, int nt, float eps,
+                          float *acc, float *pot, cudaStream_t s);
 
 // ------------------------------------------------------------ device helpers
 __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }

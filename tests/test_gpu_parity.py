@@ -278,3 +278,36 @@ def test_plummer_1m_sampled(cuda_lib):
     rel = np.linalg.norm(acc[inp] - acc_s[bodies], axis=1) / scale
     prel = np.abs(pot[inp] - pot_s[bodies]) / np.abs(pot_s[bodies])
     assert rel.max() <= P.TOL and prel.max() <= P.TOL
+
+
+# ------------------------------------------------------- direct summation
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_direct_forces_match_oracle(cuda_lib, eps):
+    import torch
+
+    pos, _, m = ics.plummer(3000, 21)
+    tg = ics.subsample(3000, 700, 40).astype(np.int32)
+    acc, pot = cuda_lib.direct_forces(_dev(pos), _dev(m), torch.from_numpy(tg).cuda(), eps)
+    ad, pd = oracle.direct(pos, m, eps, targets=tg)
+    # magnitude of the terms, for bodies whose force nearly cancels
+    d = pos[None, :, :] - pos[tg][:, None, :]
+    r2 = (d * d).sum(-1) + eps * eps
+    r2[np.arange(len(tg)), tg] = np.inf
+    amag = (m[None, :] / r2).sum(1)
+    scale = np.maximum(np.linalg.norm(ad, axis=1), P.KAPPA * amag)
+    assert np.max(np.linalg.norm(acc.cpu().numpy() - ad, axis=1) / scale) <= P.TOL
+    assert np.max(np.abs(pot.cpu().numpy() - pd) / np.abs(pd)) <= P.TOL
+
+
+def test_autotune_keeps_error_and_picks_fastest(cuda_lib):
+    import torch
+
+    from paper_1106_1900_gb300 import autotune
+
+    pos, vel, m = ics.plummer(30000, 3)
+    P_, V_, M_ = (torch.from_numpy(a).cuda() for a in (pos, vel, m))
+    best, trials = autotune.autotune(P_, V_, M_, 0.5, 0.01, grid=[(8, 16), (16, 32)], steps=2, subsample=1024)
+    paper = next(r for r in trials if (r["n_leaf"], r["n_crit"]) == autotune.PAPER_PAIR)
+    assert best["p99"] <= paper["p99"] * 1.05
+    assert best["ms_per_step"] == min(r["ms_per_step"] for r in trials if r["p99"] <= paper["p99"] * 1.05)
+    assert 1e-6 < paper["p50"] < 1e-3  # a quadrupole tree at theta = 0.5
