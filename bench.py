@@ -229,7 +229,7 @@ def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
     ctxs = []
     for s_ in range(n_sys):
         lo, hi = int(off[s_]), int(off[s_ + 1])
-        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048)
+        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048, list_capacity=4096)
         tc.set_state(P[lo:hi], V[lo:hi], M[lo:hi])
         ctxs.append((lo, hi, tc))
     for _ in range(warmup):

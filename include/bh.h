@@ -40,7 +40,8 @@ typedef enum bh_status_code {
     BH_OK = 0,
     BH_ERR_INVALID_ARG = 1, /* bad pointer, size, parameter or offsets */
     BH_ERR_CAPACITY = 2,    /* n or n_sys above the context's maxima, or a walk
-                               stack overflowed (raise stack_capacity) */
+                               stack, a group's list or the list pool overflowed
+                               (raise stack_capacity, list_capacity, pool_per_body) */
     BH_ERR_NONFINITE = 3,   /* a position or mass is NaN or infinite */
     BH_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
     BH_ERR_CUDA = 5,        /* a CUDA runtime call failed */
@@ -59,17 +60,22 @@ typedef struct bh_params {
     int32_t walk_variant;   /* 0: FP32 in group-relative coordinates with compensated
                                accumulation across list tiles (default);
                                1: naive FP32 (absolute coordinates, plain sums) */
-    int32_t walk_warps;     /* warps per walk block, 1..4, default 4 */
-    int32_t walk_blocks_per_sm; /* persistent walk grid = SMs x this; 0 = occupancy */
-    int32_t reserved[2];    /* must be 0 */
+    int32_t walk_warps;     /* warps per walk block: 4 (the walk kernels are compiled for it) */
+    int32_t walk_blocks_per_sm; /* persistent grids = SMs x this; 0 = occupancy */
+    int32_t list_capacity;  /* longest cell list and longest particle list of one
+                               group (§2.2 interaction lists), default 16384 */
+    int32_t pool_per_body;  /* interaction-list pool entries per body (the lists of
+                               all groups of one walk), default 768 */
 } bh_params;
 
 typedef struct bh_ctx bh_ctx; /* opaque, library-owned host object */
 
 /* Number of per-phase timers reported by bh_phase_times. */
-#define BH_NPHASES 8
+#define BH_NPHASES 9
 /* Phases: 0 frame+keys, 1 sort, 2 move, 3 cells+link+groups, 4 moments,
- *         5 walk, 6 leapfrog (predict+correct), 7 whole call. */
+ *         5 walk (opening radii + traversal + evaluation), 6 leapfrog
+ *         (predict+correct), 7 whole call, 8 the evaluation kernel alone
+ *         (part of 5). */
 
 /* Writes the defaults into *p.  Returns BH_OK or BH_ERR_INVALID_ARG (p NULL). */
 int bh_default_params(bh_params *p);

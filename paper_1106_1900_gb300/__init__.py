@@ -28,8 +28,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--ftz=true", "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
 BH_OK = 0
-BH_NPHASES = 8
-PHASES = ("frame+keys", "sort", "move", "cells+link+groups", "moments", "walk", "leapfrog", "call")
+BH_NPHASES = 9
+PHASES = ("frame+keys", "sort", "move", "cells+link+groups", "moments", "walk", "leapfrog", "call",
+          "walk eval")
 STATUS = {
     0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "non-finite input",
     4: "bounded device wait gave up", 5: "CUDA runtime error", 6: "call order violated",
@@ -97,7 +98,8 @@ class bh_params(ctypes.Structure):
         ("walk_variant", ctypes.c_int32),
         ("walk_warps", ctypes.c_int32),
         ("walk_blocks_per_sm", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("list_capacity", ctypes.c_int32),
+        ("pool_per_body", ctypes.c_int32),
     ]
 
 

@@ -35,8 +35,9 @@ int validate_params(const bh_params *p) {
   if (p->n_crit < p->n_leaf || p->n_crit > 64) return BH_ERR_INVALID_ARG;
   if (p->stack_capacity < 64) return BH_ERR_INVALID_ARG;
   if (p->walk_variant < 0 || p->walk_variant > 1) return BH_ERR_INVALID_ARG;
-  if (p->walk_warps < 1 || p->walk_warps > 4) return BH_ERR_INVALID_ARG;  // the walk is compiled for <= 128 threads
+  if (p->walk_warps != 4) return BH_ERR_INVALID_ARG;  // the walk kernels are compiled for 4-warp blocks
   if (p->walk_blocks_per_sm < 0 || p->walk_blocks_per_sm > 64) return BH_ERR_INVALID_ARG;
+  if (p->list_capacity < 64 || p->pool_per_body < 1) return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
 
@@ -65,17 +66,23 @@ int plan(Ctx &c, const bh_params *p, int64_t n_max, int32_t s_max, int device) {
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return BH_ERR_CUDA;
   c.num_sms = prop.multiProcessorCount;
-  c.walk_smem = bh::walk_smem_bytes(p->walk_warps);
-  int bps = p->walk_blocks_per_sm;
-  if (bps == 0) {
-    int dev0 = 0;
+  c.walk_smem = bh::walk_smem_bytes(bh::walk_block_warps());
+  int tb = p->walk_blocks_per_sm, eb = p->walk_blocks_per_sm;
+  {
+    int dev0 = 0, t_occ = 1, e_occ = 1;
     cudaGetDevice(&dev0);
     cudaSetDevice(device);
-    bps = bh::walk_max_blocks_per_sm(p->walk_warps, c.walk_smem);
+    bh::walk_grids(&t_occ, &e_occ);
     cudaSetDevice(dev0);
+    if (tb == 0) tb = t_occ;
+    if (eb == 0) eb = e_occ;
   }
-  c.walk_grid = c.num_sms * bps;
-  c.walk_warps_total = c.walk_grid * p->walk_warps;
+  // a small system needs fewer traversal warps (each owns stack and list scratch)
+  const int64_t want = std::max<int64_t>(c.num_sms, (n_max + 63) / 64);
+  c.trav_grid = (int)std::min<int64_t>((int64_t)c.num_sms * tb, want);
+  c.eval_grid = (int)std::min<int64_t>((int64_t)c.num_sms * eb, want);
+  c.trav_warps_total = c.trav_grid * bh::walk_block_warps();
+  c.pool_cap = std::max<int64_t>((int64_t)p->pool_per_body * n_max, 1ll << 22);
   c.sort_max_passes = bh::sort_passes_for(s_max);
   c.sort_tiles_max = bh::sort_tiles_for(n_max);
   return BH_OK;
@@ -134,8 +141,12 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.sort_tile_ctr = k.take<uint32_t>((size_t)c.sort_max_passes);
   c.scan_blocks = k.take<uint32_t>(std::max(R, N) / 4096 + 2);
   c.scan_total = k.take<uint64_t>(1);
-  c.walk_stack = k.take<int32_t>((size_t)c.walk_warps_total * 2 * (size_t)c.p.stack_capacity);
-  c.walk_queue = k.take<uint32_t>(1);
+  c.walk_stack = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.stack_capacity);
+  c.list_scratch = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.list_capacity);
+  c.list_pool = k.take<uint32_t>((size_t)c.pool_cap);
+  c.pool_ctr = k.take<unsigned long long>(1);
+  c.g_list = k.take<int4>(N);
+  c.walk_queue = k.take<uint32_t>(2);
   c.d_counts = k.take<int32_t>(4);
   c.d_totals = k.take<unsigned long long>(4);
   c.d_status = k.take<int32_t>(1);
@@ -293,6 +304,8 @@ int bh_default_params(bh_params *p) {
   p->walk_variant = 0;
   p->walk_warps = 4;
   p->walk_blocks_per_sm = 0;
+  p->list_capacity = 16384;
+  p->pool_per_body = 768;
   return BH_OK;
 }
 

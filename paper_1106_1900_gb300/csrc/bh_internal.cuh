@@ -27,9 +27,11 @@ struct Ctx {
   int64_t n_max = 0;
   int32_t s_max = 1;
   int64_t c_max = 0;   // cell-table bound
-  int walk_grid = 0;   // persistent walk blocks
-  int walk_warps_total = 0;
+  int trav_grid = 0;   // persistent traversal blocks
+  int eval_grid = 0;   // persistent evaluation blocks
+  int trav_warps_total = 0;
   int walk_smem = 0;
+  int64_t pool_cap = 0;  // interaction-list pool entries
   size_t ws_bytes = 0;
   char *ws = nullptr;
 
@@ -86,8 +88,12 @@ struct Ctx {
   uint32_t *scan_blocks;         // [blocks]
   uint64_t *scan_total;          // [1]
   // walk
-  int32_t *walk_stack;           // [warps][2][cap]
-  uint32_t *walk_queue;          // [1]
+  int32_t *walk_stack;           // [traversal warps][2][stack_capacity]
+  int32_t *list_scratch;         // [traversal warps][2][list_capacity]
+  uint32_t *list_pool;           // [pool_cap] every group's cell list then particle list
+  unsigned long long *pool_ctr;  // [1]
+  int4 *g_list;                  // [G] {pool offset, cells, bodies, 0}
+  uint32_t *walk_queue;          // [2] traversal, evaluation
   // scalars
   int32_t *d_counts;             // [0] C, [1] G, [2] max level
   unsigned long long *d_totals;  // [0] pp, [1] pc, [2] walk launches
@@ -129,9 +135,10 @@ cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s);
 enum OutMode { kOutCaller = 0, kOutSorted = 1 };
 cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s);
 int walk_smem_bytes(int warps);
+void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm);
+int walk_block_warps();
 cudaError_t walk_init_attrs(int smem);
 cudaError_t build_init_attrs();
-int walk_max_blocks_per_sm(int warps, int smem);
 // k_integrate.cu
 cudaError_t launch_predict(Ctx &c, double dt, cudaStream_t s);
 cudaError_t launch_correct(Ctx &c, double dt, cudaStream_t s);

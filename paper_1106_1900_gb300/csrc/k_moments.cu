@@ -179,9 +179,14 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
 // Opening radius of Eq. 1 for this theta: r_open = l/theta + delta, beside the
 // centre of mass (high part) that the walk's opening test reads.
 __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ counts, const float4 *__restrict__ mom,
-                                                float inv_theta, float4 *mac, uint32_t *queue) {
+                                                float inv_theta, float4 *mac, uint32_t *queue,
+                                                unsigned long long *pool_ctr) {
   const int C = counts[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) *queue = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the walk's group counters and list pool start empty
+    queue[0] = 0;
+    queue[1] = 0;
+    *pool_ctr = 0;
+  }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     float4 a = mom[4 * (size_t)c];
     float delta = mom[4 * (size_t)c + 1].w;
@@ -208,7 +213,7 @@ cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
 
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s) {
   float inv = (theta > 0.f) ? 1.0f / theta : INFINITY;
-  k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue);
+  k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr);
   c.launches++;
   return cudaGetLastError();
 }

@@ -1,24 +1,31 @@
 // k_walk.cu -- the breadth-first group walk and force evaluation (§2.2, §3.3).
 //
-// One warp walks one group (<= 64 bodies) at a time; warps take groups from
-// a global counter (a persistent kernel), so the walk has no block-wide
-// barrier at all.  Per group:
+// The paper walks and evaluates in one kernel: a group's interaction lists
+// fill shared memory and are evaluated whenever a tile is full.  On a GB300
+// the two halves want different machines: the walk is a chain of dependent
+// L2 reads (it wants many resident warps and few registers), the evaluation
+// is FP32 arithmetic (it wants registers for its targets and accumulators and
+// a prefetched next tile).  So they are two persistent kernels here:
 //
-//  * every lane holds two target slots, 64 per warp.  A group of n bodies
-//    gets k = floor(64/n) slots per body (one for n > 32): slot s holds body
-//    s mod n and takes every k-th source starting at s div n, and the slots of
-//    a body are summed when the group ends -- the paper's "several threads
-//    per particle" for small groups, generalised so that few slots idle.
-//  * the current level of the walk is read 32 cells at a time from a
-//    per-warp stack in global memory; each lane applies Eq. 1 to one cell
-//    (d^2 > (l/theta + delta)^2, d = distance from the cell's centre of mass
-//    to the group's bounding box).  Accepted cells are appended to the
-//    cell list, opened nodes push their (contiguous) children on the next
-//    level's stack, opened leaves append their (contiguous) bodies to the
-//    particle list; the appends are warp ballots and warp prefix sums.
-//  * whenever a list holds 32 entries they are staged in shared memory and
-//    every lane sums the 32 interactions on its slots; the remainders are
-//    flushed when the walk ends.
+//  k_traverse  one warp per group (groups taken from a counter).  The current
+//              level of the walk is read 32 cells at a time from a per-warp
+//              stack in global memory; each lane applies Eq. 1 to one cell
+//              (d^2 > (l/theta + delta)^2, d = distance from the cell's centre
+//              of mass to the group's bounding box).  Accepted cells go to the
+//              cell list, opened nodes push their (contiguous) children on the
+//              next level's stack, opened leaves append their (contiguous)
+//              bodies to the particle list; appends are warp ballots and warp
+//              prefix sums.  The lists are written to per-warp scratch, then
+//              copied into one pool at an exact offset (one atomic per group).
+//  k_eval      one warp per group.  Lists are read 32 entries at a time; the
+//              next tile's entries are gathered into registers while the
+//              current tile (staged in shared memory) is summed.
+//
+// Slots: every lane holds two target slots, 64 per warp.  A group of n bodies
+// gets k = floor(64/n) slots per body (one for n > 32): slot s holds body
+// s mod n and takes every k-th source starting at s div n, and the slots of a
+// body are summed when the group ends -- the paper's "several threads per
+// particle" for small groups, generalised so that few slots idle.
 //
 // Precision (variant 0): coordinates are offsets from the group centre c (a
 // float: the first body's position), each kept as two floats -- the rounded
@@ -39,52 +46,18 @@
 namespace bh {
 namespace {
 
-struct WarpSmem {
-  int clist[64];
-  int plist[64];
-  // staged cells: (dx, dy, dz, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0); entries >= 32 stay null
-  float4 sc[64][3];
-  // staged bodies: (S_hi, m), (S_lo, 0) -- offsets from the group centre as two floats;
-  // reused for the per-slot partial sums when a group ends (then re-nulled)
-  float4 sp[64][2];
-  int pidx[64];  // their sorted indices (read only for tiles holding the group's own bodies)
-  float box[6];  // group bounding box (min xyz, max xyz), offsets from the centre
-  float ctr[3];  // group centre
-};
-
-struct WalkArgs {
-  const float4 *__restrict__ part_hi;
-  const float4 *__restrict__ part_lo;
-  const float4 *__restrict__ mac;
-  const int2 *__restrict__ link;
-  const float4 *__restrict__ mom;
-  const int32_t *__restrict__ g_beg;
-  const int32_t *__restrict__ g_sys;
-  const int32_t *__restrict__ sys_root;
-  const int32_t *__restrict__ counts;
-  int32_t *stack;
-  int cap;
-  int n;
-  float eps2;
-  uint32_t *queue;
-  float4 *acc_sorted;
-  float *acc_out;
-  float *pot_out;
-  const uint32_t *__restrict__ perm;
-  int32_t *g_npc;
-  int32_t *g_npp;
-  unsigned long long *g_csum;
-  unsigned long long *g_psum;
-  unsigned long long *totals;
-  int32_t *status;
-};
-
 constexpr float kFar = 1e18f;
-constexpr int kWalkThreads = 128;  // 4 warps per block
-constexpr int kWalkMinBlocks = 5;  // 20 resident warps per SM (96 registers)
+constexpr int kWarps = 4;  // warps per block of both kernels
+constexpr int kThreads = 32 * kWarps;
+constexpr int kEvalMinBlocks = 5;
 
 struct Acc {
   float x, y, z, p;
+};
+
+struct Target {
+  float hx, hy, hz;  // offset from the group centre, rounded
+  float lx, ly, lz;  // its residual (variant 0) so that hi + lo is the offset to ~2^-48
 };
 
 __device__ __forceinline__ void two_sum_into(float &hi, float &lo, float v) {
@@ -104,6 +77,268 @@ __device__ __forceinline__ float two_diff(float a, float b, float &err) {
 }
 
 template <int VAR>
+__device__ __forceinline__ Target make_target(float4 h, float4 l, float cx, float cy, float cz) {
+  Target t;
+  if (VAR == 0) {
+    float ex, ey, ez;
+    t.hx = two_diff(h.x, cx, ex);
+    t.hy = two_diff(h.y, cy, ey);
+    t.hz = two_diff(h.z, cz, ez);
+    t.lx = ex + l.x;
+    t.ly = ey + l.y;
+    t.lz = ez + l.z;
+  } else {
+    t.hx = h.x;
+    t.hy = h.y;
+    t.hz = h.z;
+    t.lx = t.ly = t.lz = 0.f;
+  }
+  return t;
+}
+
+// ================================================================ traversal
+struct TravArgs {
+  const float4 *__restrict__ part_hi;
+  const float4 *__restrict__ part_lo;
+  const float4 *__restrict__ mac;
+  const int2 *__restrict__ link;
+  const int32_t *__restrict__ g_beg;
+  const int32_t *__restrict__ g_sys;
+  const int32_t *__restrict__ sys_root;
+  const int32_t *__restrict__ counts;
+  int32_t *stack;
+  int cap;
+  int32_t *scratch;  // [warps][2][list_cap]
+  int list_cap;
+  uint32_t *pool;
+  unsigned long long pool_cap;
+  unsigned long long *pool_ctr;
+  int4 *g_list;  // per group: {pool offset, cells, bodies, 0}
+  int n;
+  uint32_t *queue;
+  int32_t *g_npc;
+  int32_t *g_npp;
+  unsigned long long *g_csum;
+  unsigned long long *g_psum;
+  unsigned long long *totals;
+  int32_t *status;
+};
+
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
+  const int lane = threadIdx.x & 31;
+  const size_t gw = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  int *cur = A.stack + gw * 2 * (size_t)A.cap;
+  int *nxt = cur + A.cap;
+  int *cl = A.scratch + gw * 2 * (size_t)A.list_cap;
+  int *pl = cl + A.list_cap;
+  const unsigned lt = lanemask_lt();
+  const int G = A.counts[1];
+
+  while (true) {
+    int g = 0;
+    if (lane == 0) g = (int)atomicAdd(A.queue, 1u);
+    g = __shfl_sync(kFull, g, 0);
+    if (g >= G) break;
+    const int gb = A.g_beg[g];
+    const int n = A.g_beg[g + 1] - gb;
+    // group centre and tight bounding box (offsets from the centre, rounded)
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+    if (VAR == 0) {
+      const float4 c = A.part_hi[gb];
+      cx = c.x;
+      cy = c.y;
+      cz = c.z;
+    }
+    float bminx = INFINITY, bminy = INFINITY, bminz = INFINITY;
+    float bmaxx = -INFINITY, bmaxy = -INFINITY, bmaxz = -INFINITY;
+    for (int b = lane; b < n; b += 32) {
+      const Target t = make_target<VAR>(A.part_hi[gb + b], A.part_lo[gb + b], cx, cy, cz);
+      bminx = fminf(bminx, t.hx);
+      bminy = fminf(bminy, t.hy);
+      bminz = fminf(bminz, t.hz);
+      bmaxx = fmaxf(bmaxx, t.hx);
+      bmaxy = fmaxf(bmaxy, t.hy);
+      bmaxz = fmaxf(bmaxz, t.hz);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      bminx = fminf(bminx, __shfl_xor_sync(kFull, bminx, o));
+      bminy = fminf(bminy, __shfl_xor_sync(kFull, bminy, o));
+      bminz = fminf(bminz, __shfl_xor_sync(kFull, bminz, o));
+      bmaxx = fmaxf(bmaxx, __shfl_xor_sync(kFull, bmaxx, o));
+      bmaxy = fmaxf(bmaxy, __shfl_xor_sync(kFull, bmaxy, o));
+      bmaxz = fmaxf(bmaxz, __shfl_xor_sync(kFull, bmaxz, o));
+    }
+    int ncell = 0, npart = 0;
+    unsigned long long csum = 0, psum = 0;
+    bool full = false;
+    // ---- breadth-first walk from the root of the group's system (§2.2)
+    if (lane == 0) cur[0] = A.sys_root[A.g_sys[g]];
+    __syncwarp();
+    int ncur = 1;
+    int *cstk = cur, *nstk = nxt;
+    int depth = 0;
+    while (ncur > 0) {
+      if (++depth > kLevels + 1) {  // a tree has at most 21 levels: never loop on a corrupt one
+        if (lane == 0) set_status(A.status, BH_ERR_STATE);
+        break;
+      }
+      int nnext = 0;
+      // the frontier is read 32 cells at a time; the next chunk's loads are
+      // issued before this chunk is processed (software pipelining)
+      int ci_n = 0;
+      float4 m_n = make_float4(0.f, 0.f, 0.f, 0.f);
+      int2 lk_n = make_int2(0, 0);
+      if (lane < ncur) {
+        ci_n = cstk[lane];
+        m_n = A.mac[ci_n];
+        lk_n = A.link[ci_n];
+      }
+      int ci_nn = (32 + lane < ncur) ? cstk[32 + lane] : 0;  // stack entries run a chunk further ahead
+      for (int base = 0; base < ncur; base += 32) {
+        const bool have = base + lane < ncur;
+        const int ci = ci_n;
+        const float4 m = m_n;
+        const int2 lk = lk_n;
+        if (base + 32 + lane < ncur) {
+          ci_n = ci_nn;
+          m_n = A.mac[ci_n];
+          lk_n = A.link[ci_n];
+        }
+        if (base + 64 + lane < ncur) ci_nn = cstk[base + 64 + lane];
+        const float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
+        const float ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
+        const float ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy), 0.f);
+        const float ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz), 0.f);
+        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const bool accept = have && d2 > m.w * m.w;
+        const bool open = have && !accept;
+        const bool leaf = lk.y < 0;
+        // accepted cells -> cell list
+        const unsigned ab = __ballot_sync(kFull, accept);
+        if (accept) {
+          const int at = ncell + __popc(ab & lt);
+          if (at < A.list_cap) cl[at] = ci;
+          csum += (unsigned long long)ci;
+        }
+        ncell += __popc(ab);
+        // opened nodes -> children on the next level
+        const int nch = (open && !leaf) ? min(max(lk.y, 0), 8) : 0;
+        int inc = nch;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, inc, o);
+          if (lane >= o) inc += y;
+        }
+        const int tot = __shfl_sync(kFull, inc, 31);
+        if (nnext + tot <= A.cap) {
+          for (int j = 0; j < nch; ++j) nstk[nnext + inc - nch + j] = lk.x + j;
+          nnext += tot;
+        } else if (tot > 0) {
+          if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
+        }
+        // opened leaves -> their bodies on the particle list
+        const int np = (open && leaf) ? (lk.y & 0x7fffffff) : 0;
+        int pin = np;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, pin, o);
+          if (lane >= o) pin += y;
+        }
+        int ptot = __shfl_sync(kFull, pin, 31);
+        if (ptot < 0 || ptot > A.n) {  // more bodies than exist: a corrupt link word
+          if (lane == 0) set_status(A.status, BH_ERR_STATE);
+          ptot = 0;
+        }
+        const int pex = pin - np;
+        for (int cb = 0; cb < ptot; cb += 32) {
+          const int si = cb + lane;
+          int kk = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(kFull, pin, kk + step - 1);
+            if (v <= si) kk += step;
+          }
+          const int of = __shfl_sync(kFull, lk.x, kk);
+          const int oe = __shfl_sync(kFull, pex, kk);
+          if (si < ptot) {
+            const int body = of + (si - oe);
+            const int at = npart + si;
+            if (at < A.list_cap) pl[at] = body;
+            psum += (unsigned long long)body;
+          }
+        }
+        npart += ptot;
+      }
+      __syncwarp();
+      int *t = cstk;
+      cstk = nstk;
+      nstk = t;
+      ncur = nnext;
+    }
+    if (ncell > A.list_cap || npart > A.list_cap) {
+      full = true;
+      if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
+    }
+    // ---- copy the lists into the pool at an exact offset
+    const int nc = min(ncell, A.list_cap), npp = min(npart, A.list_cap);
+    unsigned long long off = 0;
+    if (lane == 0) off = atomicAdd(A.pool_ctr, (unsigned long long)(nc + npp));
+    off = __shfl_sync(kFull, off, 0);
+    if (off + (unsigned long long)(nc + npp) > A.pool_cap) {
+      full = true;
+      if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
+    }
+    __syncwarp();
+    if (!full) {
+      for (int i = lane; i < nc; i += 32) A.pool[off + i] = (uint32_t)cl[i];
+      for (int i = lane; i < npp; i += 32) A.pool[off + nc + i] = (uint32_t)pl[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      csum += __shfl_xor_sync(kFull, csum, o);
+      psum += __shfl_xor_sync(kFull, psum, o);
+    }
+    if (lane == 0) {
+      A.g_list[g] = full ? make_int4(0, 0, 0, 0) : make_int4((int)off, nc, npp, 0);
+      A.g_npc[g] = ncell;
+      A.g_npp[g] = npart;
+      A.g_csum[g] = csum;
+      A.g_psum[g] = psum;
+      // every body of the group is on its own particle list once (its own
+      // leaves are always opened for theta < 1.15): that self pair is not counted
+      const unsigned long long self = (npart >= n) ? (unsigned long long)n : 0ull;
+      atomicAdd(&A.totals[0], (unsigned long long)n * (unsigned long long)npart - self);
+      atomicAdd(&A.totals[1], (unsigned long long)n * (unsigned long long)ncell);
+    }
+    __syncwarp();
+  }
+}
+
+// =============================================================== evaluation
+struct EvalSmem {
+  // staged cells: (dx, dy, dz, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0); entries >= 32 stay null
+  float4 sc[64][3];
+  // staged bodies: (S_hi, m), (S_lo, 0); reused for the per-slot sums when a
+  // group ends (entries >= 32 are re-nulled afterwards)
+  float4 sp[64][2];
+  int pidx[64];  // their sorted indices (read only for tiles holding the group's own bodies)
+};
+
+struct EvalArgs {
+  const float4 *__restrict__ part_hi;
+  const float4 *__restrict__ part_lo;
+  const float4 *__restrict__ mom;
+  const int32_t *__restrict__ g_beg;
+  const int4 *__restrict__ g_list;
+  const uint32_t *__restrict__ pool;
+  const int32_t *__restrict__ counts;
+  float eps2;
+  uint32_t *queue;
+  float4 *acc_sorted;
+  float *acc_out;
+  float *pot_out;
+  const uint32_t *__restrict__ perm;
+};
+
+template <int VAR>
 __device__ __forceinline__ void fold(Acc &hi, Acc &lo, Acc &t) {
   if (VAR == 0) {
     two_sum_into(hi.x, lo.x, t.x);
@@ -118,11 +353,6 @@ __device__ __forceinline__ void fold(Acc &hi, Acc &lo, Acc &t) {
   }
   t = Acc{0.f, 0.f, 0.f, 0.f};
 }
-
-struct Target {
-  float hx, hy, hz;  // offset from the group centre, rounded
-  float lx, ly, lz;  // its residual (variant 0) so that hi + lo is the offset to ~2^-48
-};
 
 // Softened particle-particle interaction of a staged source (S_hi, m), S_lo on
 // a target: 20 flops by the convention FMA = 2, rsqrt = 1 (the two-float
@@ -149,8 +379,8 @@ __device__ __forceinline__ void pp(Acc &a, const Target &t, const float4 sh, con
   float ri = rsqrtf(r2);
   if (GUARD) ri = (r2 > 0.f) ? ri : 0.f;
   if (SELF) ri = (me == other) ? 0.f : ri;
-  float mr = sh.w * ri;
-  float mr3 = mr * ri * ri;
+  const float mr = sh.w * ri;
+  const float mr3 = mr * ri * ri;
   a.p -= mr;
   a.x = fmaf(mr3, dx, a.x);
   a.y = fmaf(mr3, dy, a.y);
@@ -162,57 +392,32 @@ __device__ __forceinline__ void pp(Acc &a, const Target &t, const float4 sh, con
 // 54 flops by the convention above.
 __device__ __forceinline__ void pc(Acc &a, const Target &t, const float4 c0, const float4 q0, const float4 q1,
                                    float eps2) {
-  float dx = c0.x - t.hx, dy = c0.y - t.hy, dz = c0.z - t.hz;
+  const float dx = c0.x - t.hx, dy = c0.y - t.hy, dz = c0.z - t.hz;
   float r2 = fmaf(dx, dx, eps2);
   r2 = fmaf(dy, dy, r2);
   r2 = fmaf(dz, dz, r2);
-  float ri = rsqrtf(r2);
-  float ri2 = ri * ri;
-  float mr = c0.w * ri;
-  float mr3 = mr * ri2;
-  float qx = fmaf(q1.x, dz, fmaf(q0.w, dy, q0.x * dx));
-  float qy = fmaf(q1.y, dz, fmaf(q0.y, dy, q0.w * dx));
-  float qz = fmaf(q0.z, dz, fmaf(q1.y, dy, q1.x * dx));
-  float dqd = fmaf(qz, dz, fmaf(qy, dy, qx * dx));
-  float ri5 = ri2 * ri2 * ri;
-  float qr5 = dqd * ri5;
+  const float ri = rsqrtf(r2);
+  const float ri2 = ri * ri;
+  const float mr = c0.w * ri;
+  const float mr3 = mr * ri2;
+  const float qx = fmaf(q1.x, dz, fmaf(q0.w, dy, q0.x * dx));
+  const float qy = fmaf(q1.y, dz, fmaf(q0.y, dy, q0.w * dx));
+  const float qz = fmaf(q0.z, dz, fmaf(q1.y, dy, q1.x * dx));
+  const float dqd = fmaf(qz, dz, fmaf(qy, dy, qx * dx));
+  const float ri5 = ri2 * ri2 * ri;
+  const float qr5 = dqd * ri5;
   a.p = fmaf(-0.5f, qr5, a.p - mr);
-  float coef = fmaf(2.5f * qr5, ri2, mr3);
+  const float coef = fmaf(2.5f * qr5, ri2, mr3);
   a.x = fmaf(-ri5, qx, fmaf(coef, dx, a.x));
   a.y = fmaf(-ri5, qy, fmaf(coef, dy, a.y));
   a.z = fmaf(-ri5, qz, fmaf(coef, dz, a.z));
 }
 
-template <int VAR>
-__device__ __forceinline__ Target make_target(float4 h, float4 l, float cx, float cy, float cz) {
-  Target t;
-  if (VAR == 0) {
-    float ex, ey, ez;
-    t.hx = two_diff(h.x, cx, ex);
-    t.hy = two_diff(h.y, cy, ey);
-    t.hz = two_diff(h.z, cz, ez);
-    t.lx = ex + l.x;
-    t.ly = ey + l.y;
-    t.lz = ez + l.z;
-  } else {
-    t.hx = h.x;
-    t.hy = h.y;
-    t.hz = h.z;
-    t.lx = t.ly = t.lz = 0.f;
-  }
-  return t;
-}
-
 template <int VAR, bool GUARD, int MODE>
-__global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks) k_walk(WalkArgs A) {
-  extern __shared__ WarpSmem s_warp[];
+__global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
+  extern __shared__ EvalSmem s_eval[];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  WarpSmem &S = s_warp[wib];
-  const size_t gw = (size_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  int *cur = A.stack + gw * 2 * (size_t)A.cap;
-  int *nxt = cur + A.cap;
-  const unsigned lt = lanemask_lt();
+  EvalSmem &S = s_eval[threadIdx.x >> 5];
   const float eps2 = A.eps2;
   const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -233,9 +438,9 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks) k_walk(WalkArgs 
     if (g >= G) break;
     const int gb = A.g_beg[g];
     const int n = A.g_beg[g + 1] - gb;
-    const int root = A.sys_root[A.g_sys[g]];
-    // slots: a group of n bodies gets k = floor(64/n) slots per body (one for
-    // n > 32); slot s holds body s % n and takes the sources j = s / n (mod k)
+    const int4 L = A.g_list[g];
+    const uint32_t *clist = A.pool + (unsigned)L.x;
+    const uint32_t *plist = clist + L.y;
     const int k = (n > 32) ? 1 : min(64 / n, 32);
     int b0, b1, ph0, ph1;
     bool v0, v1;
@@ -254,10 +459,9 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks) k_walk(WalkArgs 
       ph0 = v0 ? lane / n : 0;
       ph1 = v1 ? (lane + 32) / n : 0;
     }
-    // group centre (a float: the first body) and the slots' targets
     float cx = 0.f, cy = 0.f, cz = 0.f;
     if (VAR == 0) {
-      float4 c = A.part_hi[gb];
+      const float4 c = A.part_hi[gb];
       cx = c.x;
       cy = c.y;
       cz = c.z;
@@ -265,243 +469,140 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks) k_walk(WalkArgs 
     const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
     const Target T0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
     const Target T1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
-    // tight bounding box of the group's bodies
-    float bminx = fminf(v0 ? T0.hx : INFINITY, v1 ? T1.hx : INFINITY);
-    float bminy = fminf(v0 ? T0.hy : INFINITY, v1 ? T1.hy : INFINITY);
-    float bminz = fminf(v0 ? T0.hz : INFINITY, v1 ? T1.hz : INFINITY);
-    float bmaxx = fmaxf(v0 ? T0.hx : -INFINITY, v1 ? T1.hx : -INFINITY);
-    float bmaxy = fmaxf(v0 ? T0.hy : -INFINITY, v1 ? T1.hy : -INFINITY);
-    float bmaxz = fmaxf(v0 ? T0.hz : -INFINITY, v1 ? T1.hz : -INFINITY);
-    for (int o = 16; o > 0; o >>= 1) {
-      bminx = fminf(bminx, __shfl_xor_sync(kFull, bminx, o));
-      bminy = fminf(bminy, __shfl_xor_sync(kFull, bminy, o));
-      bminz = fminf(bminz, __shfl_xor_sync(kFull, bminz, o));
-      bmaxx = fmaxf(bmaxx, __shfl_xor_sync(kFull, bmaxx, o));
-      bmaxy = fmaxf(bmaxy, __shfl_xor_sync(kFull, bmaxy, o));
-      bmaxz = fmaxf(bmaxz, __shfl_xor_sync(kFull, bmaxz, o));
-    }
-    if (lane == 0) {
-      S.box[0] = bminx;
-      S.box[1] = bminy;
-      S.box[2] = bminz;
-      S.box[3] = bmaxx;
-      S.box[4] = bmaxy;
-      S.box[5] = bmaxz;
-      S.ctr[0] = cx;
-      S.ctr[1] = cy;
-      S.ctr[2] = cz;
-    }
-    __syncwarp();
     Acc h0 = {0, 0, 0, 0}, l0 = {0, 0, 0, 0}, h1 = {0, 0, 0, 0}, l1 = {0, 0, 0, 0};
     Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};  // partial sums since the last fold
     int since = 0;                              // interactions per slot since the last fold
-    int cn = 0, pn = 0, ncell = 0, npart = 0;
-    unsigned long long csum = 0, psum = 0;
 
-    auto after_tile = [&](int cnt) {
-      since += (cnt + k - 1) / k;
-      if (since >= 32) {
-        fold<VAR>(h0, l0, t0);
-        fold<VAR>(h1, l1, t1);
-        since = 0;
+    // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
+    {
+      const int nc = L.y;
+      // indices run one tile ahead of the gathers, which run one tile ahead of
+      // the arithmetic: no gather waits on the load of its own address
+      float4 ra = zero4, rb = zero4, rq0 = zero4, rq1 = zero4;
+      if (lane < nc) {
+        const size_t ci = clist[lane];
+        ra = A.mom[4 * ci];
+        rb = A.mom[4 * ci + 1];
+        rq0 = A.mom[4 * ci + 2];
+        rq1 = A.mom[4 * ci + 3];
       }
-    };
-
-    // ---- evaluate the first `cnt` entries of the cell list
-    auto eval_cells = [&](int cnt) {
-      if (lane < cnt) {
-        int cc = S.clist[lane];
-        float4 a = A.mom[4 * (size_t)cc], b = A.mom[4 * (size_t)cc + 1];
-        float4 q0 = A.mom[4 * (size_t)cc + 2], q1 = A.mom[4 * (size_t)cc + 3];
-        float dx, dy, dz;
-        if (VAR == 0) {
-          dx = (a.x - S.ctr[0]) + b.x;
-          dy = (a.y - S.ctr[1]) + b.y;
-          dz = (a.z - S.ctr[2]) + b.z;
+      uint32_t ci_next = (32 + lane < nc) ? clist[32 + lane] : 0u;
+      for (int base = 0; base < nc; base += 32) {
+        const int cnt = min(32, nc - base);
+        if (lane < cnt) {
+          float dx, dy, dz;
+          if (VAR == 0) {
+            dx = (ra.x - cx) + rb.x;
+            dy = (ra.y - cy) + rb.y;
+            dz = (ra.z - cz) + rb.z;
+          } else {
+            dx = ra.x;
+            dy = ra.y;
+            dz = ra.z;
+          }
+          S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
+          S.sc[lane][1] = rq0;
+          S.sc[lane][2] = make_float4(rq1.x, rq1.y, 0.f, 0.f);
         } else {
-          dx = a.x;
-          dy = a.y;
-          dz = a.z;
+          S.sc[lane][0] = null_src;
+          S.sc[lane][1] = zero4;
+          S.sc[lane][2] = zero4;
         }
-        S.sc[lane][0] = make_float4(dx, dy, dz, a.w);
-        S.sc[lane][1] = q0;
-        S.sc[lane][2] = make_float4(q1.x, q1.y, 0.f, 0.f);
-      } else {
-        S.sc[lane][0] = null_src;
-        S.sc[lane][1] = zero4;
-        S.sc[lane][2] = zero4;
-      }
-      __syncwarp();
-      if (k == 1) {
-#pragma unroll 1
-        for (int j = 0; j < cnt; ++j) {
-          const float4 c0 = S.sc[j][0], q0 = S.sc[j][1], q1 = S.sc[j][2];
-          pc(t0, T0, c0, q0, q1, eps2);
-          pc(t1, T1, c0, q0, q1, eps2);
+        if (base + 32 + lane < nc) {  // gather the next tile now
+          const size_t ci = ci_next;
+          ra = A.mom[4 * ci];
+          rb = A.mom[4 * ci + 1];
+          rq0 = A.mom[4 * ci + 2];
+          rq1 = A.mom[4 * ci + 3];
         }
-      } else {
-#pragma unroll 1
-        for (int j = 0; j < cnt; j += k) {
-          pc(t0, T0, S.sc[j + ph0][0], S.sc[j + ph0][1], S.sc[j + ph0][2], eps2);
-          pc(t1, T1, S.sc[j + ph1][0], S.sc[j + ph1][1], S.sc[j + ph1][2], eps2);
-        }
-      }
-      after_tile(cnt);
-      __syncwarp();
-    };
-
-    // ---- evaluate the first `cnt` entries of the particle list
-    auto eval_bodies = [&](int cnt) {
-      bool member = false;
-      if (lane < cnt) {
-        int b = S.plist[lane];
-        member = (unsigned)(b - gb) < (unsigned)n;
-        const Target s = make_target<VAR>(A.part_hi[b], A.part_lo[b], S.ctr[0], S.ctr[1], S.ctr[2]);
-        S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, A.part_hi[b].w);
-        S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
-        S.pidx[lane] = b;
-      } else {
-        S.sp[lane][0] = null_src;
-        S.sp[lane][1] = zero4;
-        S.pidx[lane] = -1;
-      }
-      const bool self_tile = __any_sync(kFull, member);
-      __syncwarp();
-      if (self_tile) {
-        // a tile with the group's own bodies: skip each body's pair with itself by index
-        const int me0 = gb + b0, me1 = gb + b1;
-        for (int j = 0; j < cnt; j += k) {
-          pp<VAR, GUARD, true>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2, me0, S.pidx[j + ph0]);
-          pp<VAR, GUARD, true>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2, me1, S.pidx[j + ph1]);
-        }
-      } else if (k == 1) {
-#pragma unroll 2
-        for (int j = 0; j < cnt; ++j) {
-          const float4 sh = S.sp[j][0], sl = S.sp[j][1];
-          pp<VAR, GUARD, false>(t0, T0, sh, sl, eps2);
-          pp<VAR, GUARD, false>(t1, T1, sh, sl, eps2);
-        }
-      } else {
-#pragma unroll 2
-        for (int j = 0; j < cnt; j += k) {
-          pp<VAR, GUARD, false>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2);
-          pp<VAR, GUARD, false>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2);
-        }
-      }
-      after_tile(cnt);
-      __syncwarp();
-    };
-
-    // ---- breadth-first walk (§2.2)
-    if (lane == 0) cur[0] = root;
-    __syncwarp();
-    int ncur = 1;
-    int *cstk = cur, *nstk = nxt;
-    int depth = 0;
-    while (ncur > 0) {
-      if (++depth > kLevels + 1) {  // a tree has at most 21 levels: never loop on a corrupt one
-        if (lane == 0) set_status(A.status, BH_ERR_STATE);
-        break;
-      }
-      int nnext = 0;
-      for (int base = 0; base < ncur; base += 32) {
-        const bool have = base + lane < ncur;
-        int ci = 0;
-        float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
-        int2 lk = make_int2(0, 0);
-        if (have) {
-          ci = cstk[base + lane];
-          m = A.mac[ci];
-          lk = A.link[ci];
-        }
-        float rx = m.x - S.ctr[0], ry = m.y - S.ctr[1], rz = m.z - S.ctr[2];
-        float ex = fmaxf(fmaxf(S.box[0] - rx, rx - S.box[3]), 0.f);
-        float ey = fmaxf(fmaxf(S.box[1] - ry, ry - S.box[4]), 0.f);
-        float ez = fmaxf(fmaxf(S.box[2] - rz, rz - S.box[5]), 0.f);
-        float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        const bool accept = have && d2 > m.w * m.w;
-        const bool open = have && !accept;
-        const bool leaf = lk.y < 0;
-        // accepted cells -> cell list
-        unsigned ab = __ballot_sync(kFull, accept);
-        if (accept) {
-          S.clist[cn + __popc(ab & lt)] = ci;
-          csum += (unsigned long long)ci;
-        }
-        cn += __popc(ab);
-        ncell += __popc(ab);
+        if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
         __syncwarp();
-        if (cn >= 32) {
-          eval_cells(32);
-          int tmp = (lane < cn - 32) ? S.clist[32 + lane] : 0;
-          __syncwarp();
-          if (lane < cn - 32) S.clist[lane] = tmp;
-          cn -= 32;
-          __syncwarp();
-        }
-        // opened nodes -> children on the next level
-        int nch = (open && !leaf) ? min(max(lk.y, 0), 8) : 0;
-        int inc = nch;
-        for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(kFull, inc, o);
-          if (lane >= o) inc += y;
-        }
-        const int tot = __shfl_sync(kFull, inc, 31);
-        if (nnext + tot <= A.cap) {
-          for (int j = 0; j < nch; ++j) nstk[nnext + inc - nch + j] = lk.x + j;
-          nnext += tot;
-        } else if (tot > 0) {
-          if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
-        }
-        // opened leaves -> bodies on the particle list
-        int np = (open && leaf) ? (lk.y & 0x7fffffff) : 0;
-        int pin = np;
-        for (int o = 1; o < 32; o <<= 1) {
-          int y = __shfl_up_sync(kFull, pin, o);
-          if (lane >= o) pin += y;
-        }
-        int ptot = __shfl_sync(kFull, pin, 31);
-        if (ptot < 0 || ptot > A.n) {  // more bodies than exist: a corrupt link word
-          if (lane == 0) set_status(A.status, BH_ERR_STATE);
-          ptot = 0;
-        }
-        npart += ptot;
-        const int pex = pin - np;
-        for (int cb = 0; cb < ptot; cb += 32) {
-          const int si = cb + lane;
-          int kk = 0;
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            int v = __shfl_sync(kFull, pin, kk + step - 1);
-            if (v <= si) kk += step;
+        if (k == 1) {
+#pragma unroll 1
+          for (int j = 0; j < cnt; ++j) {
+            const float4 c0 = S.sc[j][0], q0 = S.sc[j][1], q1 = S.sc[j][2];
+            pc(t0, T0, c0, q0, q1, eps2);
+            pc(t1, T1, c0, q0, q1, eps2);
           }
-          const int of = __shfl_sync(kFull, lk.x, kk);
-          const int oe = __shfl_sync(kFull, pex, kk);
-          if (si < ptot) {
-            const int body = of + (si - oe);
-            S.plist[pn + lane] = body;
-            psum += (unsigned long long)body;
-          }
-          pn += min(32, ptot - cb);
-          __syncwarp();
-          if (pn >= 32) {
-            eval_bodies(32);
-            int tmp = (lane < pn - 32) ? S.plist[32 + lane] : 0;
-            __syncwarp();
-            if (lane < pn - 32) S.plist[lane] = tmp;
-            pn -= 32;
-            __syncwarp();
+        } else {
+#pragma unroll 1
+          for (int j = 0; j < cnt; j += k) {
+            pc(t0, T0, S.sc[j + ph0][0], S.sc[j + ph0][1], S.sc[j + ph0][2], eps2);
+            pc(t1, T1, S.sc[j + ph1][0], S.sc[j + ph1][1], S.sc[j + ph1][2], eps2);
           }
         }
+        since += (cnt + k - 1) / k;
+        if (since >= 32) {
+          fold<VAR>(h0, l0, t0);
+          fold<VAR>(h1, l1, t1);
+          since = 0;
+        }
+        __syncwarp();
       }
-      __syncwarp();
-      int *t = cstk;
-      cstk = nstk;
-      nstk = t;
-      ncur = nnext;
     }
-    if (cn > 0) eval_cells(cn);
-    if (pn > 0) eval_bodies(pn);
+    // ---- particle list
+    {
+      const int np = L.z;
+      float4 rh = zero4, rl = zero4;
+      int rb = -1;
+      if (lane < np) {
+        rb = (int)plist[lane];
+        rh = A.part_hi[rb];
+        rl = A.part_lo[rb];
+      }
+      int pb_next = (32 + lane < np) ? (int)plist[32 + lane] : -1;
+      for (int base = 0; base < np; base += 32) {
+        const int cnt = min(32, np - base);
+        bool member = false;
+        if (lane < cnt) {
+          member = (unsigned)(rb - gb) < (unsigned)n;
+          const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
+          S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
+          S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
+          S.pidx[lane] = rb;
+        } else {
+          S.sp[lane][0] = null_src;
+          S.sp[lane][1] = zero4;
+          S.pidx[lane] = -1;
+        }
+        if (base + 32 + lane < np) {  // gather the next tile now
+          rb = pb_next;
+          rh = A.part_hi[rb];
+          rl = A.part_lo[rb];
+        }
+        if (base + 64 + lane < np) pb_next = (int)plist[base + 64 + lane];
+        const bool self_tile = __any_sync(kFull, member);
+        __syncwarp();
+        if (self_tile) {
+          // a tile with the group's own bodies: skip each body's pair with itself by index
+          const int me0 = gb + b0, me1 = gb + b1;
+          for (int j = 0; j < cnt; j += k) {
+            pp<VAR, GUARD, true>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2, me0, S.pidx[j + ph0]);
+            pp<VAR, GUARD, true>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2, me1, S.pidx[j + ph1]);
+          }
+        } else if (k == 1) {
+#pragma unroll 2
+          for (int j = 0; j < cnt; ++j) {
+            const float4 sh = S.sp[j][0], sl = S.sp[j][1];
+            pp<VAR, GUARD, false>(t0, T0, sh, sl, eps2);
+            pp<VAR, GUARD, false>(t1, T1, sh, sl, eps2);
+          }
+        } else {
+#pragma unroll 2
+          for (int j = 0; j < cnt; j += k) {
+            pp<VAR, GUARD, false>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2);
+            pp<VAR, GUARD, false>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2);
+          }
+        }
+        since += (cnt + k - 1) / k;
+        if (since >= 32) {
+          fold<VAR>(h0, l0, t0);
+          fold<VAR>(h1, l1, t1);
+          since = 0;
+        }
+        __syncwarp();
+      }
+    }
     fold<VAR>(h0, l0, t0);
     fold<VAR>(h1, l1, t1);
 
@@ -529,120 +630,136 @@ __global__ void __launch_bounds__(kWalkThreads, kWalkMinBlocks) k_walk(WalkArgs 
       S.sp[32 + lane][1] = make_float4(l1.x, l1.y, l1.z, l1.p);
       __syncwarp();
       if (lane < n) {
-        float4 H = S.sp[lane][0], L = S.sp[lane][1];
+        float4 H = S.sp[lane][0], Lo = S.sp[lane][1];
         for (int q = 1; q < k; ++q) {
           const float4 h = S.sp[lane + q * n][0], l = S.sp[lane + q * n][1];
-          two_sum_into(H.x, L.x, h.x);
-          two_sum_into(H.y, L.y, h.y);
-          two_sum_into(H.z, L.z, h.z);
-          two_sum_into(H.w, L.w, h.w);
-          L.x += l.x;
-          L.y += l.y;
-          L.z += l.z;
-          L.w += l.w;
+          two_sum_into(H.x, Lo.x, h.x);
+          two_sum_into(H.y, Lo.y, h.y);
+          two_sum_into(H.z, Lo.z, h.z);
+          two_sum_into(H.w, Lo.w, h.w);
+          Lo.x += l.x;
+          Lo.y += l.y;
+          Lo.z += l.z;
+          Lo.w += l.w;
         }
-        write_body(lane, H.x + L.x, H.y + L.y, H.z + L.z, H.w + L.w);
+        write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
       }
       __syncwarp();
       S.sp[32 + lane][0] = null_src;
       S.sp[32 + lane][1] = zero4;
       __syncwarp();
     }
-    // ---- group statistics
-    for (int o = 16; o > 0; o >>= 1) {
-      csum += __shfl_xor_sync(kFull, csum, o);
-      psum += __shfl_xor_sync(kFull, psum, o);
-    }
-    if (lane == 0) {
-      A.g_npc[g] = ncell;
-      A.g_npp[g] = npart;
-      A.g_csum[g] = csum;
-      A.g_psum[g] = psum;
-      // every body of the group is on its own particle list once (its own
-      // leaves are always opened for theta < 1.15): that self pair is not counted
-      const unsigned long long self = (npart >= n) ? (unsigned long long)n : 0ull;
-      atomicAdd(&A.totals[0], (unsigned long long)n * (unsigned long long)npart - self);
-      atomicAdd(&A.totals[1], (unsigned long long)n * (unsigned long long)ncell);
-    }
   }
 }
 
 template <int VAR, bool GUARD, int MODE>
-cudaError_t launch_one(Ctx &c, const WalkArgs &a, cudaStream_t s) {
-  k_walk<VAR, GUARD, MODE><<<c.walk_grid, c.p.walk_warps * 32, c.walk_smem, s>>>(a);
+cudaError_t launch_eval(Ctx &c, const EvalArgs &a, cudaStream_t s) {
+  k_eval<VAR, GUARD, MODE><<<c.eval_grid, kThreads, kWarps * sizeof(EvalSmem), s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int walk_smem_bytes(int warps) { return warps * (int)sizeof(WarpSmem); }
+int walk_smem_bytes(int warps) { return warps * (int)sizeof(EvalSmem); }
 
 cudaError_t walk_init_attrs(int smem) {
   cudaError_t e = cudaSuccess;
-#define BH_WALK_ATTR(V, G, M) \
-  if (!e) e = cudaFuncSetAttribute(k_walk<V, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  BH_WALK_ATTR(0, false, kOutCaller)
-  BH_WALK_ATTR(0, true, kOutCaller)
-  BH_WALK_ATTR(0, false, kOutSorted)
-  BH_WALK_ATTR(0, true, kOutSorted)
-  BH_WALK_ATTR(1, false, kOutCaller)
-  BH_WALK_ATTR(1, true, kOutCaller)
-  BH_WALK_ATTR(1, false, kOutSorted)
-  BH_WALK_ATTR(1, true, kOutSorted)
-#undef BH_WALK_ATTR
+#define BH_EVAL_ATTR(V, G, M) \
+  if (!e) e = cudaFuncSetAttribute(k_eval<V, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  BH_EVAL_ATTR(0, false, kOutCaller)
+  BH_EVAL_ATTR(0, true, kOutCaller)
+  BH_EVAL_ATTR(0, false, kOutSorted)
+  BH_EVAL_ATTR(0, true, kOutSorted)
+  BH_EVAL_ATTR(1, false, kOutCaller)
+  BH_EVAL_ATTR(1, true, kOutCaller)
+  BH_EVAL_ATTR(1, false, kOutSorted)
+  BH_EVAL_ATTR(1, true, kOutSorted)
+#undef BH_EVAL_ATTR
   return e;
 }
 
-int walk_max_blocks_per_sm(int warps, int smem) {
-  int nb = 0;
-  cudaFuncSetAttribute(k_walk<0, false, kOutCaller>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_walk<0, false, kOutCaller>, warps * 32, smem) !=
+void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm) {
+  int nt = 0, ne = 0;
+  const int smem = kWarps * (int)sizeof(EvalSmem);
+  cudaFuncSetAttribute(k_eval<0, false, kOutCaller>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, k_traverse<0>, kThreads, 0) != cudaSuccess) nt = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ne, k_eval<0, false, kOutCaller>, kThreads, smem) !=
       cudaSuccess)
-    return 1;
-  return nb > 0 ? nb : 1;
+    ne = 1;
+  *trav_blocks_per_sm = nt > 0 ? nt : 1;
+  *eval_blocks_per_sm = ne > 0 ? ne : 1;
 }
 
+int walk_block_warps() { return kWarps; }
+
 cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s) {
-  WalkArgs a;
+  TravArgs t;
+  t.part_hi = c.part_hi;
+  t.part_lo = c.part_lo;
+  t.mac = c.c_mac;
+  t.link = c.c_link;
+  t.g_beg = c.g_beg;
+  t.g_sys = c.g_sys;
+  t.sys_root = c.sys_root;
+  t.counts = c.d_counts;
+  t.stack = c.walk_stack;
+  t.cap = c.p.stack_capacity;
+  t.scratch = c.list_scratch;
+  t.list_cap = c.p.list_capacity;
+  t.pool = c.list_pool;
+  t.pool_cap = (unsigned long long)c.pool_cap;
+  t.pool_ctr = c.pool_ctr;
+  t.g_list = c.g_list;
+  t.n = (int)c.n;
+  t.queue = c.walk_queue;
+  t.g_npc = c.g_npc;
+  t.g_npp = c.g_npp;
+  t.g_csum = c.g_csum;
+  t.g_psum = c.g_psum;
+  t.totals = c.d_totals;
+  t.status = c.d_status;
+  const int var = c.p.walk_variant;
+  if (var == 0) k_traverse<0><<<c.trav_grid, kThreads, 0, s>>>(t);
+  else k_traverse<1><<<c.trav_grid, kThreads, 0, s>>>(t);
+  cudaError_t e = cudaGetLastError();
+  c.launches++;
+  if (e) return e;
+  if (c.profiling) {
+    if (c.capturing) cudaEventRecordWithFlags(c.ev[8][0], s, cudaEventRecordExternal);
+    else cudaEventRecord(c.ev[8][0], s);
+  }
+  EvalArgs a;
   a.part_hi = c.part_hi;
   a.part_lo = c.part_lo;
-  a.mac = c.c_mac;
-  a.link = c.c_link;
   a.mom = c.c_mom;
   a.g_beg = c.g_beg;
-  a.g_sys = c.g_sys;
-  a.sys_root = c.sys_root;
+  a.g_list = c.g_list;
+  a.pool = c.list_pool;
   a.counts = c.d_counts;
-  a.stack = c.walk_stack;
-  a.cap = c.p.stack_capacity;
-  a.n = (int)c.n;
   a.eps2 = eps * eps;
-  a.queue = c.walk_queue;
+  a.queue = c.walk_queue + 1;
   a.acc_sorted = c.acc_sorted;
   a.acc_out = acc;
   a.pot_out = pot;
   a.perm = c.idx[0];
-  a.g_npc = c.g_npc;
-  a.g_npp = c.g_npp;
-  a.g_csum = c.g_csum;
-  a.g_psum = c.g_psum;
-  a.totals = c.d_totals;
-  a.status = c.d_status;
   const bool guard = !(a.eps2 > 0.f);
-  const int var = c.p.walk_variant;
-  cudaError_t e;
-#define BH_WALK_CASE(V, G, M) \
-  if (var == V && guard == G && mode == M) e = launch_one<V, G, M>(c, a, s); else
-  BH_WALK_CASE(0, false, kOutCaller)
-  BH_WALK_CASE(0, true, kOutCaller)
-  BH_WALK_CASE(0, false, kOutSorted)
-  BH_WALK_CASE(0, true, kOutSorted)
-  BH_WALK_CASE(1, false, kOutCaller)
-  BH_WALK_CASE(1, true, kOutCaller)
-  BH_WALK_CASE(1, false, kOutSorted)
-  BH_WALK_CASE(1, true, kOutSorted)
+#define BH_EVAL_CASE(V, G, M) \
+  if (var == V && guard == G && mode == M) e = launch_eval<V, G, M>(c, a, s); else
+  BH_EVAL_CASE(0, false, kOutCaller)
+  BH_EVAL_CASE(0, true, kOutCaller)
+  BH_EVAL_CASE(0, false, kOutSorted)
+  BH_EVAL_CASE(0, true, kOutSorted)
+  BH_EVAL_CASE(1, false, kOutCaller)
+  BH_EVAL_CASE(1, true, kOutCaller)
+  BH_EVAL_CASE(1, false, kOutSorted)
+  BH_EVAL_CASE(1, true, kOutSorted)
   e = cudaErrorInvalidValue;
-#undef BH_WALK_CASE
+#undef BH_EVAL_CASE
+  if (c.profiling) {
+    if (c.capturing) cudaEventRecordWithFlags(c.ev[8][1], s, cudaEventRecordExternal);
+    else cudaEventRecord(c.ev[8][1], s);
+    c.phase_rec[8] = true;
+  }
   c.launches++;
   return e;
 }
