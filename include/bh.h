@@ -59,7 +59,8 @@ typedef struct bh_params {
                                warp (§2.2 current/next-level stacks), default 16384 */
     int32_t walk_variant;   /* 0: FP32 in group-relative coordinates with compensated
                                accumulation across list tiles (default);
-                               1: naive FP32 (absolute coordinates, plain sums) */
+                               1: naive FP32 (absolute coordinates, plain sums);
+                               2: FP64 evaluation (a slow precision reference) */
     int32_t walk_warps;     /* warps per walk block: 4 (the walk kernels are compiled for it) */
     int32_t walk_blocks_per_sm; /* persistent grids = SMs x this; 0 = occupancy */
     int32_t list_capacity;  /* longest cell list and longest particle list of one

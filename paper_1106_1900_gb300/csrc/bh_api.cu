@@ -34,7 +34,7 @@ int validate_params(const bh_params *p) {
   if (p->n_leaf < 1 || p->n_leaf > 64) return BH_ERR_INVALID_ARG;
   if (p->n_crit < p->n_leaf || p->n_crit > 64) return BH_ERR_INVALID_ARG;
   if (p->stack_capacity < 64) return BH_ERR_INVALID_ARG;
-  if (p->walk_variant < 0 || p->walk_variant > 1) return BH_ERR_INVALID_ARG;
+  if (p->walk_variant < 0 || p->walk_variant > 2) return BH_ERR_INVALID_ARG;
   if (p->walk_warps != 4) return BH_ERR_INVALID_ARG;  // the walk kernels are compiled for 4-warp blocks
   if (p->walk_blocks_per_sm < 0 || p->walk_blocks_per_sm > 64) return BH_ERR_INVALID_ARG;
   if (p->list_capacity < 64 || p->pool_per_body < 1) return BH_ERR_INVALID_ARG;

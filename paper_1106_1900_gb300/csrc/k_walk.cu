@@ -652,6 +652,78 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
   }
 }
 
+// FP64 evaluation of the same lists (walk variant 2, a precision reference on
+// the GPU: GB300's FP64 rate is a small fraction of its FP32 rate, so this is a
+// study variant, not a fast path).  One warp per group, a lane per body (two
+// for n > 32), positions recombined from their two-float form (~2^-48 relative),
+// moments as stored (FP32), every operation in FP64.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_eval_f64(EvalArgs A) {
+  const int lane = threadIdx.x & 31;
+  const double eps2 = (double)A.eps2;
+  const int G = A.counts[1];
+  while (true) {
+    int g = 0;
+    if (lane == 0) g = (int)atomicAdd(A.queue, 1u);
+    g = __shfl_sync(kFull, g, 0);
+    if (g >= G) break;
+    const int gb = A.g_beg[g];
+    const int n = A.g_beg[g + 1] - gb;
+    const int4 L = A.g_list[g];
+    const uint32_t *clist = A.pool + (unsigned)L.x;
+    const uint32_t *plist = clist + L.y;
+    for (int b = lane; b < n; b += 32) {
+      const float4 th = A.part_hi[gb + b], tl = A.part_lo[gb + b];
+      const double tx = (double)th.x + (double)tl.x, ty = (double)th.y + (double)tl.y,
+                   tz = (double)th.z + (double)tl.z;
+      double ax = 0, ay = 0, az = 0, ap = 0;
+      for (int j = 0; j < L.y; ++j) {
+        const size_t c = clist[j];
+        const float4 a = A.mom[4 * c], lo = A.mom[4 * c + 1], q0 = A.mom[4 * c + 2], q1 = A.mom[4 * c + 3];
+        const double dx = ((double)a.x + (double)lo.x) - tx, dy = ((double)a.y + (double)lo.y) - ty,
+                     dz = ((double)a.z + (double)lo.z) - tz;
+        const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+        const double ri = 1.0 / sqrt(r2), ri2 = ri * ri, ri5 = ri2 * ri2 * ri;
+        const double qx = (double)q0.x * dx + (double)q0.w * dy + (double)q1.x * dz;
+        const double qy = (double)q0.w * dx + (double)q0.y * dy + (double)q1.y * dz;
+        const double qz = (double)q1.x * dx + (double)q1.y * dy + (double)q0.z * dz;
+        const double dqd = qx * dx + qy * dy + qz * dz;
+        const double mr = (double)a.w * ri;
+        const double coef = mr * ri2 + 2.5 * dqd * ri5 * ri2;
+        ax += coef * dx - ri5 * qx;
+        ay += coef * dy - ri5 * qy;
+        az += coef * dz - ri5 * qz;
+        ap += -mr - 0.5 * dqd * ri5;
+      }
+      for (int j = 0; j < L.z; ++j) {
+        const int s = (int)plist[j];
+        if (s == gb + b) continue;
+        const float4 sh = A.part_hi[s], sl = A.part_lo[s];
+        const double dx = ((double)sh.x + (double)sl.x) - tx, dy = ((double)sh.y + (double)sl.y) - ty,
+                     dz = ((double)sh.z + (double)sl.z) - tz;
+        const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+        if (!(r2 > 0.0)) continue;
+        const double ri = 1.0 / sqrt(r2);
+        const double mr = (double)sh.w * ri, mr3 = mr * ri * ri;
+        ax += mr3 * dx;
+        ay += mr3 * dy;
+        az += mr3 * dz;
+        ap -= mr;
+      }
+      const int gi = gb + b;
+      if (MODE == kOutSorted) {
+        A.acc_sorted[gi] = make_float4((float)ax, (float)ay, (float)az, (float)ap);
+      } else {
+        const size_t o = A.perm[gi];
+        A.acc_out[3 * o] = (float)ax;
+        A.acc_out[3 * o + 1] = (float)ay;
+        A.acc_out[3 * o + 2] = (float)az;
+        A.pot_out[o] = (float)ap;
+      }
+    }
+  }
+}
+
 template <int VAR, bool GUARD, int MODE>
 cudaError_t launch_eval(Ctx &c, const EvalArgs &a, cudaStream_t s) {
   k_eval<VAR, GUARD, MODE><<<c.eval_grid, kThreads, kWarps * sizeof(EvalSmem), s>>>(a);
@@ -719,8 +791,8 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   t.totals = c.d_totals;
   t.status = c.d_status;
   const int var = c.p.walk_variant;
-  if (var == 0) k_traverse<0><<<c.trav_grid, kThreads, 0, s>>>(t);
-  else k_traverse<1><<<c.trav_grid, kThreads, 0, s>>>(t);
+  if (var == 1) k_traverse<1><<<c.trav_grid, kThreads, 0, s>>>(t);
+  else k_traverse<0><<<c.trav_grid, kThreads, 0, s>>>(t);
   cudaError_t e = cudaGetLastError();
   c.launches++;
   if (e) return e;
@@ -743,6 +815,11 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   a.pot_out = pot;
   a.perm = c.idx[0];
   const bool guard = !(a.eps2 > 0.f);
+  if (var == 2) {
+    if (mode == kOutSorted) k_eval_f64<kOutSorted><<<c.eval_grid, kThreads, 0, s>>>(a);
+    else k_eval_f64<kOutCaller><<<c.eval_grid, kThreads, 0, s>>>(a);
+    e = cudaGetLastError();
+  } else
 #define BH_EVAL_CASE(V, G, M) \
   if (var == V && guard == G && mode == M) e = launch_eval<V, G, M>(c, a, s); else
   BH_EVAL_CASE(0, false, kOutCaller)

@@ -256,16 +256,15 @@ def test_forest_step_equals_systems(cuda_lib):
         assert np.allclose(vf[b:e], vs, rtol=0, atol=1e-9)
 
 
-# ------------------------------------------------- full-size (1M) sampled
-def test_plummer_1m_sampled(cuda_lib):
-    """The benchmark's workload: integer tables bit-exact, forces on every
-    400th group against the oracle walking the same groups."""
-    pos, _, m = ics.plummer(1 << 20, 2)
-    tc, acc, pot = _run(cuda_lib, pos, m, 0.5, 0.005)
-    t = oracle.build_tree(pos, m)
+# --------------------------------------------- full-size workloads, sampled
+def _sampled_parity(bh, pos, m, theta, eps, every, offsets=None, **kw):
+    """Integer tables bit-exact; forces of every `every`-th group against the
+    oracle walking the same groups (the launch configuration of bench.py)."""
+    tc, acc, pot = _run(bh, pos, m, theta, eps, offsets=offsets, **kw)
+    t = oracle.build_tree(pos, m, offsets=offsets)
     P.compare_tree(tc.tree(), t)
-    groups = np.arange(0, t.G, 400)
-    acc_s, pot_s, st = oracle.walk(t, 0.5, 0.005, groups)
+    groups = np.arange(0, t.G, every)
+    acc_s, pot_s, st = oracle.walk(t, theta, eps, groups)
     gst = tc.group_stats()
     sub = {k: v[groups] for k, v in gst.items()}
     same = (sub["nc"] == st["nc"]) & (sub["np"] == st["np"]) & (sub["csum"] == st["csum"]) & (
@@ -278,6 +277,28 @@ def test_plummer_1m_sampled(cuda_lib):
     rel = np.linalg.norm(acc[inp] - acc_s[bodies], axis=1) / scale
     prel = np.abs(pot[inp] - pot_s[bodies]) / np.abs(pot_s[bodies])
     assert rel.max() <= P.TOL and prel.max() <= P.TOL
+    return t, int((~same).sum())
+
+
+def test_plummer_1m_sampled(cuda_lib):
+    """The benchmark's workload (configs[1]): 2^20-body Plummer sphere, theta = 0.5."""
+    pos, _, m = ics.plummer(1 << 20, 2)
+    _sampled_parity(cuda_lib, pos, m, 0.5, 0.005, every=400)
+
+
+def test_galaxy_8m_sampled(cuda_lib):
+    """Hernquist sphere + exponential disk, 8,388,608 bodies (configs[2]): a sparse,
+    very non-uniform tree."""
+    pos, _, m = ics.galaxy(4194304, 4194304, 3)
+    t, flipped = _sampled_parity(cuda_lib, pos, m, 0.5, 0.01, every=3000, pool_per_body=512)
+    assert np.bincount(t.level).size > 12  # a deep tree
+
+
+def test_ensemble_7m_sampled(cuda_lib):
+    """512 Plummer clusters, ~7.7M bodies in one forest (configs[4])."""
+    pos, _, m, off = ics.ensemble(512, 5)
+    t, flipped = _sampled_parity(cuda_lib, pos, m, 0.5, 0.01, every=3000, offsets=off, pool_per_body=512)
+    assert t.sys_root.min() >= 0
 
 
 # ------------------------------------------------------- direct summation
