@@ -92,6 +92,7 @@ struct Ctx {
   int32_t *list_scratch;         // [traversal warps][2][list_capacity]
   uint32_t *list_pool;           // [pool_cap] every group's cell list then particle list
   unsigned long long *pool_ctr;  // [1]
+  unsigned long long *work_total;  // [1] estimated evaluation cost of this walk
   int4 *g_list;                  // [G] {pool offset, cells, bodies, 0}
   uint32_t *walk_queue;          // [2] traversal, evaluation
   // scalars

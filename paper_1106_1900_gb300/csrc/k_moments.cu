@@ -185,7 +185,8 @@ __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ coun
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // the walk's group counters and list pool start empty
     queue[0] = 0;
     queue[1] = 0;
-    *pool_ctr = 0;
+    pool_ctr[0] = 0;  // list pool offset
+    pool_ctr[1] = 0;  // total estimated evaluation cost
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     float4 a = mom[4 * (size_t)c];

@@ -49,7 +49,7 @@ namespace {
 constexpr float kFar = 1e18f;
 constexpr int kWarps = 4;  // warps per block of both kernels
 constexpr int kThreads = 32 * kWarps;
-constexpr int kEvalMinBlocks = 5;
+constexpr int kEvalMinBlocks = 6;
 
 struct Acc {
   float x, y, z, p;
@@ -113,7 +113,8 @@ struct TravArgs {
   uint32_t *pool;
   unsigned long long pool_cap;
   unsigned long long *pool_ctr;
-  int4 *g_list;  // per group: {pool offset, cells, bodies, 0}
+  int4 *g_list;  // per group: {pool offset, cells, bodies, estimated evaluation cost}
+  unsigned long long *work_total;  // sum of the estimates of this launch
   int n;
   uint32_t *queue;
   int32_t *g_npc;
@@ -297,7 +298,11 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       psum += __shfl_xor_sync(kFull, psum, o);
     }
     if (lane == 0) {
-      A.g_list[g] = full ? make_int4(0, 0, 0, 0) : make_int4((int)off, nc, npp, 0);
+      // evaluation cost ~ (2 cells + 1 body per list entry) / slots per body
+      const int k = (n > 32) ? 1 : min(64 / n, 32);
+      const int work = (2 * nc + npp + k - 1) / k + 1;
+      A.g_list[g] = full ? make_int4(0, 0, 0, 1) : make_int4((int)off, nc, npp, work);
+      atomicAdd(A.work_total, (unsigned long long)work);
       A.g_npc[g] = ncell;
       A.g_npp[g] = npart;
       A.g_csum[g] = csum;
@@ -316,10 +321,11 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
 struct EvalSmem {
   // staged cells: (dx, dy, dz, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0); entries >= 32 stay null
   float4 sc[64][3];
-  // staged bodies: (S_hi, m), (S_lo, 0); reused for the per-slot sums when a
-  // group ends (entries >= 32 are re-nulled afterwards)
+  // staged bodies: (S_hi, m), (S_lo, 0); entries >= 32 stay null
   float4 sp[64][2];
   int pidx[64];  // their sorted indices (read only for tiles holding the group's own bodies)
+  float4 ah[64];  // per slot: compensated sum (hi part) of acceleration and potential
+  float4 al[64];  // per slot: its lo part
 };
 
 struct EvalArgs {
@@ -330,6 +336,7 @@ struct EvalArgs {
   const int4 *__restrict__ g_list;
   const uint32_t *__restrict__ pool;
   const int32_t *__restrict__ counts;
+  const unsigned long long *__restrict__ work_total;
   float eps2;
   uint32_t *queue;
   float4 *acc_sorted;
@@ -338,19 +345,24 @@ struct EvalArgs {
   const uint32_t *__restrict__ perm;
 };
 
+// Fold a slot's partial sum into its compensated (hi, lo) pair, which lives in
+// shared memory (touched once per ~32 interactions, so not worth registers).
 template <int VAR>
-__device__ __forceinline__ void fold(Acc &hi, Acc &lo, Acc &t) {
+__device__ __forceinline__ void fold(float4 &hs, float4 &ls, Acc &t) {
+  float4 hi = hs, lo = ls;
   if (VAR == 0) {
     two_sum_into(hi.x, lo.x, t.x);
     two_sum_into(hi.y, lo.y, t.y);
     two_sum_into(hi.z, lo.z, t.z);
-    two_sum_into(hi.p, lo.p, t.p);
+    two_sum_into(hi.w, lo.w, t.p);
+    ls = lo;
   } else {
     hi.x += t.x;
     hi.y += t.y;
     hi.z += t.z;
-    hi.p += t.p;
+    hi.w += t.p;
   }
+  hs = hi;
   t = Acc{0.f, 0.f, 0.f, 0.f};
 }
 
@@ -430,15 +442,21 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
   S.pidx[32 + lane] = -1;
   __syncwarp();
   const int G = A.counts[1];
+  // longest first, coarsely: one sweep over the groups for those that cost more
+  // than twice the mean, then one for the rest, so that the launch does not end
+  // waiting on a few expensive groups taken last
+  const unsigned long long heavy = 2 * (*A.work_total) / (unsigned long long)max(G, 1);
 
   while (true) {
-    int g = 0;
-    if (lane == 0) g = (int)atomicAdd(A.queue, 1u);
-    g = __shfl_sync(kFull, g, 0);
-    if (g >= G) break;
+    int q = 0;
+    if (lane == 0) q = (int)atomicAdd(A.queue, 1u);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= 2 * G) break;
+    const int g = (q < G) ? q : q - G;
+    const int4 L = A.g_list[g];
+    if ((q < G) != ((unsigned long long)L.w > heavy)) continue;
     const int gb = A.g_beg[g];
     const int n = A.g_beg[g + 1] - gb;
-    const int4 L = A.g_list[g];
     const uint32_t *clist = A.pool + (unsigned)L.x;
     const uint32_t *plist = clist + L.y;
     const int k = (n > 32) ? 1 : min(64 / n, 32);
@@ -469,7 +487,10 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
     const Target T0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
     const Target T1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
-    Acc h0 = {0, 0, 0, 0}, l0 = {0, 0, 0, 0}, h1 = {0, 0, 0, 0}, l1 = {0, 0, 0, 0};
+    S.ah[lane] = zero4;
+    S.al[lane] = zero4;
+    S.ah[32 + lane] = zero4;
+    S.al[32 + lane] = zero4;
     Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};  // partial sums since the last fold
     int since = 0;                              // interactions per slot since the last fold
 
@@ -533,8 +554,8 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
         }
         since += (cnt + k - 1) / k;
         if (since >= 32) {
-          fold<VAR>(h0, l0, t0);
-          fold<VAR>(h1, l1, t1);
+          fold<VAR>(S.ah[lane], S.al[lane], t0);
+          fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
           since = 0;
         }
         __syncwarp();
@@ -596,15 +617,16 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
         }
         since += (cnt + k - 1) / k;
         if (since >= 32) {
-          fold<VAR>(h0, l0, t0);
-          fold<VAR>(h1, l1, t1);
+          fold<VAR>(S.ah[lane], S.al[lane], t0);
+          fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
           since = 0;
         }
         __syncwarp();
       }
     }
-    fold<VAR>(h0, l0, t0);
-    fold<VAR>(h1, l1, t1);
+    fold<VAR>(S.ah[lane], S.al[lane], t0);
+    fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+    __syncwarp();
 
     // ---- combine the slots of each body and write
     auto write_body = [&](int b, float ox, float oy, float oz, float op) {
@@ -620,19 +642,20 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
       }
     };
     if (k == 1) {
-      if (v0) write_body(b0, h0.x + l0.x, h0.y + l0.y, h0.z + l0.z, h0.p + l0.p);
-      if (v1) write_body(b1, h1.x + l1.x, h1.y + l1.y, h1.z + l1.z, h1.p + l1.p);
+      if (v0) {
+        const float4 H = S.ah[lane], Lo = S.al[lane];
+        write_body(b0, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+      }
+      if (v1) {
+        const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
+        write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+      }
     } else {
-      // slot s -> sp[s] = (hi), (lo); body b sums slots b, b + n, ..., b + n (k - 1)
-      S.sp[lane][0] = make_float4(h0.x, h0.y, h0.z, h0.p);
-      S.sp[lane][1] = make_float4(l0.x, l0.y, l0.z, l0.p);
-      S.sp[32 + lane][0] = make_float4(h1.x, h1.y, h1.z, h1.p);
-      S.sp[32 + lane][1] = make_float4(l1.x, l1.y, l1.z, l1.p);
-      __syncwarp();
+      // body b sums the compensated pairs of its slots b, b + n, ..., b + n (k - 1)
       if (lane < n) {
-        float4 H = S.sp[lane][0], Lo = S.sp[lane][1];
+        float4 H = S.ah[lane], Lo = S.al[lane];
         for (int q = 1; q < k; ++q) {
-          const float4 h = S.sp[lane + q * n][0], l = S.sp[lane + q * n][1];
+          const float4 h = S.ah[lane + q * n], l = S.al[lane + q * n];
           two_sum_into(H.x, Lo.x, h.x);
           two_sum_into(H.y, Lo.y, h.y);
           two_sum_into(H.z, Lo.z, h.z);
@@ -644,11 +667,8 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
         }
         write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
       }
-      __syncwarp();
-      S.sp[32 + lane][0] = null_src;
-      S.sp[32 + lane][1] = zero4;
-      __syncwarp();
     }
+    __syncwarp();
   }
 }
 
@@ -672,7 +692,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_f64(EvalArgs A) {
     const int4 L = A.g_list[g];
     const uint32_t *clist = A.pool + (unsigned)L.x;
     const uint32_t *plist = clist + L.y;
-    for (int b = lane; b < n; b += 32) {
+    for (int b = lane; b < n; b += 32) {  // (one sweep: this study variant is not tuned)
       const float4 th = A.part_hi[gb + b], tl = A.part_lo[gb + b];
       const double tx = (double)th.x + (double)tl.x, ty = (double)th.y + (double)tl.y,
                    tz = (double)th.z + (double)tl.z;
@@ -782,6 +802,7 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   t.pool_cap = (unsigned long long)c.pool_cap;
   t.pool_ctr = c.pool_ctr;
   t.g_list = c.g_list;
+  t.work_total = c.work_total;
   t.n = (int)c.n;
   t.queue = c.walk_queue;
   t.g_npc = c.g_npc;
@@ -808,6 +829,7 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   a.g_list = c.g_list;
   a.pool = c.list_pool;
   a.counts = c.d_counts;
+  a.work_total = c.work_total;
   a.eps2 = eps * eps;
   a.queue = c.walk_queue + 1;
   a.acc_sorted = c.acc_sorted;
