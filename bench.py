@@ -39,6 +39,13 @@ FLOPS_PP = 20
 FLOPS_PC = 54
 SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
+# algorithmic HBM bytes of the build phases of one step (frame + keys, sort,
+# move, cells + links + groups, moments, leapfrog predict + correct); counted
+# from what each kernel must read and write once
+BUILD_BYTES_PER_BODY = 724
+BUILD_BYTES_PER_CELL = 216
+BUILD_BYTES_PER_GROUP = 8
+HBM_FALLBACK_GBS = 6800.0
 
 
 def parse():
@@ -55,6 +62,9 @@ def parse():
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--untuned", action="store_true", help="use the paper's N_leaf = 16, N_crit = 64")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy"],
+                    help="plummer: N-body Plummer sphere (--n); galaxy: Hernquist sphere + exponential disk, "
+                         "8,388,608 bodies")
     return ap.parse_args()
 
 
@@ -326,11 +336,20 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     bh.load()
-    n = args.n
-    pos, vel, m = ics.plummer(n, SEED + rank)
+    eps = EPS
+    if args.workload == "galaxy":
+        pos, vel, m = ics.galaxy(4194304, 4194304, 3 + rank)
+        eps = 0.01
+        workload = (f"galaxy: Hernquist sphere (a=1, M=1) + exponential disk (R_d=1, z0=0.1, M=0.2), "
+                    f"N={len(pos)} per GPU (seed 3+rank), theta={args.theta}, eps={eps}, dt=1/64")
+    else:
+        pos, vel, m = ics.plummer(args.n, SEED + rank)
+        workload = (f"Plummer N={args.n} per GPU (virial units, seed {SEED}+rank), theta={args.theta}, "
+                    f"eps={EPS}, dt=1/64")
+    n = len(pos)
     from paper_1106_1900_gb300 import autotune
 
-    tuned = None if args.untuned else autotune.tuned_params(n, args.theta)
+    tuned = None if args.untuned else autotune.tuned_params(n, args.theta, args.workload)
     tc = bh.TreeCode(n, device=local, **(tuned or {}))
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
@@ -341,7 +360,7 @@ def main():
         tc.set_state(P, V, M)
         tc.set_profiling(True)
         for _ in range(args.warmup):
-            tc.step(DT, args.theta, EPS, graph=not args.eager)
+            tc.step(DT, args.theta, eps, graph=not args.eager)
         tc.check()
         torch.cuda.synchronize()
         tc.reset_counters()
@@ -357,7 +376,7 @@ def main():
                 if args.flush_mb > 0:
                     flush.fill_(k & 0xff)
                 ev[k][0].record(stream)
-                tc.step(DT, args.theta, EPS, graph=not args.eager)
+                tc.step(DT, args.theta, eps, graph=not args.eager)
                 ev[k][1].record(stream)
                 ph = tc.phase_times()  # synchronises on this step's events
                 walk_ms.append(ph["walk"])
@@ -387,6 +406,17 @@ def main():
     traffic = walk_traffic()
     clocks = clk.summary()
     mean_phase = {k: statistics.mean(p[k] for p in phases) for k in bh.PHASES if k != "call"}
+    # build phases against HBM bandwidth
+    cnt0 = tc.counts()
+    build_ms = sum(mean_phase[k] for k in ("frame+keys", "sort", "move", "cells+link+groups", "moments",
+                                           "leapfrog"))
+    build_bytes = (BUILD_BYTES_PER_BODY * n + BUILD_BYTES_PER_CELL * cnt0["cells"]
+                   + BUILD_BYTES_PER_GROUP * cnt0["groups"])
+    hbm = float(measured_peaks().get("hbm_gbs", HBM_FALLBACK_GBS))
+    build_gbs = build_bytes / (build_ms * 1e-3) / 1e9 if build_ms > 0 else 0.0
+    build = {"ms_per_step": build_ms, "algorithmic_bytes_per_step": build_bytes, "achieved_GBs": build_gbs,
+             "peak_GBs": hbm, "frac": build_gbs / hbm,
+             "peak_source": "measured" if "hbm_gbs" in measured_peaks() else "fallback"}
     # ---- end to end through the public API from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -396,22 +426,22 @@ def main():
         hq = torch.empty(n, dtype=torch.float32).pin_memory()
         tc2 = bh.TreeCode(n, device=local, **(tuned or {}))
         for _ in range(max(1, args.warmup)):
-            tc2.forces_host(hp, hm, args.theta, EPS, ha, hq, stream=stream)
+            tc2.forces_host(hp, hm, args.theta, eps, ha, hq, stream=stream)
         if world > 1:
             torch.distributed.barrier()
         e0 = time.perf_counter()
         for _ in range(args.steps):
-            tc2.forces_host(hp, hm, args.theta, EPS, ha, hq, stream=stream)
+            tc2.forces_host(hp, hm, args.theta, eps, ha, hq, stream=stream)
         e_s = max_over_ranks(time.perf_counter() - e0, world, dev)
         e2e = {"value": bodies_all / e_s, "unit": UNIT, "h2d_bytes_per_step": n * (24 + 8),
                "d2h_bytes_per_step": n * (12 + 4)}
         tc2.close()
     ens = None
-    if not args.no_ensemble:
+    if not args.no_ensemble and args.workload == "plummer":
         ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=3, warmup=2)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pos, m, args.theta, EPS)
+        cpu = cpu_baseline(pos, m, args.theta, eps)
     if rank != 0:
         return
     cnt = tc.counts()
@@ -419,8 +449,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"Plummer N={n} per GPU (virial units, seed {SEED}+rank), theta={args.theta}, "
-                               f"eps={EPS}, dt=1/64, full leapfrog step as one CUDA graph",
+        "config": {"workload": workload + ", full leapfrog step as one CUDA graph",
                    "global_batch": n * world, "parallelism": f"independent system per GPU x{world}",
                    "l2": f"flushed between timed steps ({args.flush_mb} MB write)" if args.flush_mb else "not flushed",
                    "n_leaf": tc.params.n_leaf, "n_crit": tc.params.n_crit,
@@ -437,6 +466,7 @@ def main():
                                     "frac": achieved_walk / peak if peak else None,
                                     "what": "opening radii + k_traverse + k_eval"}},
         "phase_ms_mean": mean_phase,
+        "build": build,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,

@@ -246,6 +246,18 @@ def test_graph_step_equals_eager(cuda_lib):
     assert np.array_equal(x1, x2) and np.array_equal(v1, v2) and np.array_equal(a1, a2)
 
 
+def test_checkpoint_resume_is_bit_identical(cuda_lib):
+    # 6 steps in one run == 3 steps, state copied out, loaded into a new
+    # context, 3 more steps (the tree is rebuilt from positions every step)
+    import torch
+
+    pos, vel, m = ics.plummer(20000, 33)
+    _, x6, v6, a6, _ = _state_run(cuda_lib, pos, vel, m, 6, 1 / 64, 0.5, 0.01)
+    _, x3, v3, _, _ = _state_run(cuda_lib, pos, vel, m, 3, 1 / 64, 0.5, 0.01)
+    _, xr, vr, ar, _ = _state_run(cuda_lib, x3, v3, m, 3, 1 / 64, 0.5, 0.01)
+    assert np.array_equal(x6, xr) and np.array_equal(v6, vr) and np.array_equal(a6, ar)
+
+
 def test_forest_step_equals_systems(cuda_lib):
     pos, vel, m, off = ics.ensemble(n_sys=6, seed=7, n_min=500, n_max=4000)
     _, xf, vf, _, _ = _state_run(cuda_lib, pos, vel, m, 3, 1 / 64, 0.5, 0.01, offsets=off)
