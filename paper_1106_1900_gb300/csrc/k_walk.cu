@@ -25,7 +25,10 @@
 // gets k = floor(64/n) slots per body (one for n > 32): slot s holds body
 // s mod n and takes every k-th source starting at s div n, and the slots of a
 // body are summed when the group ends -- the paper's "several threads per
-// particle" for small groups, generalised so that few slots idle.
+// particle" for small groups, generalised so that few slots idle.  A group of
+// 33..48 bodies would idle a quarter of the slots or more; it is evaluated in
+// two or three passes over the same lists, each for a subset of its bodies
+// small enough for three or four slots per body (eval_passes).
 //
 // Precision (variant 0): coordinates are offsets from the group centre c (a
 // float: the first body's position), each kept as two floats -- the rounded
@@ -76,6 +79,33 @@ __device__ __forceinline__ float two_diff(float a, float b, float &err) {
   return s;
 }
 
+// Slots per body for a (sub)group of n <= 64 bodies on the warp's 64 slots.
+__device__ __forceinline__ int slots_per_body(int n) { return (n > 32) ? 1 : min(64 / n, 32); }
+
+// Passes over a group's lists.  A group of 33..63 bodies gets one slot per
+// body and leaves 64 - n slots idle; P passes over subsets of ceil(n / P)
+// bodies each, all on the group's own lists (a list valid for a group is valid
+// for any subset of it), fill the slots better.  A pass costs ceil(32 / k)
+// iterations per 32-entry tile, but no less than ~8: below that the tile's
+// gather from L2 is no longer hidden behind its arithmetic, and every pass
+// re-gathers the lists.  So smaller groups keep one pass, and 33..42 bodies
+// take two, 43..48 three.
+__device__ __forceinline__ int eval_passes(int n) {
+  if (n <= 32) return 1;
+  int best = 1, best_cost = 1 << 30;
+  for (int P = 1; P <= 4; ++P) {
+    const int nb = (n + P - 1) / P;
+    const int k = slots_per_body(nb);
+    const int cost = P * (max((32 + k - 1) / k, 8) + 1);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = P;
+    }
+  }
+  const int nb = (n + best - 1) / best;
+  return (n + nb - 1) / nb;  // no empty last pass
+}
+
 template <int VAR>
 __device__ __forceinline__ Target make_target(float4 h, float4 l, float cx, float cy, float cz) {
   Target t;
@@ -124,6 +154,24 @@ struct TravArgs {
   unsigned long long *totals;
   int32_t *status;
 };
+
+// dst[0..cnt) = src[0..cnt), a warp, four independent loads in flight per lane
+__device__ __forceinline__ void copy_list(uint32_t *__restrict__ dst, const int *__restrict__ src, int cnt,
+                                          int lane) {
+  for (int i0 = 0; i0 < cnt; i0 += 128) {
+    int v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u + lane;
+      v[u] = (i < cnt) ? src[i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 32 * u + lane;
+      if (i < cnt) dst[i] = (uint32_t)v[u];
+    }
+  }
+}
 
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
@@ -223,28 +271,47 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
           csum += (unsigned long long)ci;
         }
         ncell += __popc(ab);
-        // opened nodes -> children on the next level
+        // opened nodes -> children on the next level, opened leaves -> bodies
         const int nch = (open && !leaf) ? min(max(lk.y, 0), 8) : 0;
-        int inc = nch;
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, inc, o);
-          if (lane >= o) inc += y;
+        const int np = (open && leaf) ? (lk.y & 0x7fffffff) : 0;
+        int inc, pin, tot, ptot;
+        if (__all_sync(kFull, np < (1 << 17))) {
+          // both prefix sums in one scan: children (<= 256 a chunk) in the low
+          // 10 bits, bodies (< 2^22 a chunk) above them
+          unsigned v = (unsigned)nch | ((unsigned)np << 10);
+          for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, v, o);
+            if (lane >= o) v += y;
+          }
+          const unsigned vt = __shfl_sync(kFull, v, 31);
+          inc = (int)(v & 1023u);
+          pin = (int)(v >> 10);
+          tot = (int)(vt & 1023u);
+          ptot = (int)(vt >> 10);
+        } else {  // a leaf of 2^17 bodies or more (coincident positions): two scans
+          inc = nch;
+          pin = np;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, inc, o);
+            const int z = __shfl_up_sync(kFull, pin, o);
+            if (lane >= o) {
+              inc += y;
+              pin += z;
+            }
+          }
+          tot = __shfl_sync(kFull, inc, 31);
+          ptot = __shfl_sync(kFull, pin, 31);
         }
-        const int tot = __shfl_sync(kFull, inc, 31);
         if (nnext + tot <= A.cap) {
-          for (int j = 0; j < nch; ++j) nstk[nnext + inc - nch + j] = lk.x + j;
+          int *dst = nstk + (nnext + inc - nch);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)  // predicated stores, no divergent loop
+            if (j < nch) dst[j] = lk.x + j;
           nnext += tot;
         } else if (tot > 0) {
           if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
         }
         // opened leaves -> their bodies on the particle list
-        const int np = (open && leaf) ? (lk.y & 0x7fffffff) : 0;
-        int pin = np;
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, pin, o);
-          if (lane >= o) pin += y;
-        }
-        int ptot = __shfl_sync(kFull, pin, 31);
         if (ptot < 0 || ptot > A.n) {  // more bodies than exist: a corrupt link word
           if (lane == 0) set_status(A.status, BH_ERR_STATE);
           ptot = 0;
@@ -290,8 +357,8 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
     }
     __syncwarp();
     if (!full) {
-      for (int i = lane; i < nc; i += 32) A.pool[off + i] = (uint32_t)cl[i];
-      for (int i = lane; i < npp; i += 32) A.pool[off + nc + i] = (uint32_t)pl[i];
+      copy_list(A.pool + off, cl, nc, lane);
+      copy_list(A.pool + off + nc, pl, npp, lane);
     }
     for (int o = 16; o > 0; o >>= 1) {
       csum += __shfl_xor_sync(kFull, csum, o);
@@ -299,8 +366,9 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
     }
     if (lane == 0) {
       // evaluation cost ~ (2 cells + 1 body per list entry) / slots per body
-      const int k = (n > 32) ? 1 : min(64 / n, 32);
-      const int work = (2 * nc + npp + k - 1) / k + 1;
+      const int P = eval_passes(n);
+      const int k = slots_per_body((n + P - 1) / P);
+      const int work = P * ((2 * nc + npp + k - 1) / k + 1);
       A.g_list[g] = full ? make_int4(0, 0, 0, 1) : make_int4((int)off, nc, npp, work);
       atomicAdd(A.work_total, (unsigned long long)work);
       A.g_npc[g] = ncell;
@@ -455,220 +523,227 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     const int g = (q < G) ? q : q - G;
     const int4 L = A.g_list[g];
     if ((q < G) != ((unsigned long long)L.w > heavy)) continue;
-    const int gb = A.g_beg[g];
-    const int n = A.g_beg[g + 1] - gb;
-    const uint32_t *clist = A.pool + (unsigned)L.x;
-    const uint32_t *plist = clist + L.y;
-    const int k = (n > 32) ? 1 : min(64 / n, 32);
-    int b0, b1, ph0, ph1;
-    bool v0, v1;
-    if (k == 1) {
-      b0 = lane;
-      b1 = lane + 32;
-      ph0 = ph1 = 0;
-      v0 = b0 < n;
-      v1 = b1 < n;
-    } else {
-      const int ns = n * k;
-      v0 = lane < ns;
-      v1 = lane + 32 < ns;
-      b0 = lane % n;
-      b1 = (lane + 32) % n;
-      ph0 = v0 ? lane / n : 0;
-      ph1 = v1 ? (lane + 32) / n : 0;
-    }
+    const int gb0 = A.g_beg[g];
+    const int ng = A.g_beg[g + 1] - gb0;
     float cx = 0.f, cy = 0.f, cz = 0.f;
     if (VAR == 0) {
-      const float4 c = A.part_hi[gb];
+      const float4 c = A.part_hi[gb0];
       cx = c.x;
       cy = c.y;
       cz = c.z;
     }
-    const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
-    const Target T0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
-    const Target T1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
-    S.ah[lane] = zero4;
-    S.al[lane] = zero4;
-    S.ah[32 + lane] = zero4;
-    S.al[32 + lane] = zero4;
-    Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};  // partial sums since the last fold
-    int since = 0;                              // interactions per slot since the last fold
-
-    // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
-    {
-      const int nc = L.y;
-      // indices run one tile ahead of the gathers, which run one tile ahead of
-      // the arithmetic: no gather waits on the load of its own address
-      float4 ra = zero4, rb = zero4, rq0 = zero4, rq1 = zero4;
-      if (lane < nc) {
-        const size_t ci = clist[lane];
-        ra = A.mom[4 * ci];
-        rb = A.mom[4 * ci + 1];
-        rq0 = A.mom[4 * ci + 2];
-        rq1 = A.mom[4 * ci + 3];
+    const int npass = eval_passes(ng);
+    const int nbp = (ng + npass - 1) / npass;
+    for (int pass = 0; pass < npass; ++pass) {
+      // this pass: bodies gb .. gb + n - 1 of the group, on the group's lists
+      const int gb = gb0 + pass * nbp;
+      const int n = min(nbp, ng - pass * nbp);
+      const int k = slots_per_body(n);
+      const uint32_t *clist = A.pool + (unsigned)L.x;
+      const uint32_t *plist = clist + L.y;
+      int b0, b1, ph0, ph1;
+      bool v0, v1;
+      if (k == 1) {
+        b0 = lane;
+        b1 = lane + 32;
+        ph0 = ph1 = 0;
+        v0 = b0 < n;
+        v1 = b1 < n;
+      } else {
+        const int ns = n * k;
+        v0 = lane < ns;
+        v1 = lane + 32 < ns;
+        b0 = lane % n;
+        b1 = (lane + 32) % n;
+        ph0 = v0 ? lane / n : 0;
+        ph1 = v1 ? (lane + 32) / n : 0;
       }
-      uint32_t ci_next = (32 + lane < nc) ? clist[32 + lane] : 0u;
-      for (int base = 0; base < nc; base += 32) {
-        const int cnt = min(32, nc - base);
-        if (lane < cnt) {
-          float dx, dy, dz;
-          if (VAR == 0) {
-            dx = (ra.x - cx) + rb.x;
-            dy = (ra.y - cy) + rb.y;
-            dz = (ra.z - cz) + rb.z;
-          } else {
-            dx = ra.x;
-            dy = ra.y;
-            dz = ra.z;
-          }
-          S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
-          S.sc[lane][1] = rq0;
-          S.sc[lane][2] = make_float4(rq1.x, rq1.y, 0.f, 0.f);
-        } else {
-          S.sc[lane][0] = null_src;
-          S.sc[lane][1] = zero4;
-          S.sc[lane][2] = zero4;
-        }
-        if (base + 32 + lane < nc) {  // gather the next tile now
-          const size_t ci = ci_next;
+      const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
+      const Target T0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
+      const Target T1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
+      S.ah[lane] = zero4;
+      S.al[lane] = zero4;
+      S.ah[32 + lane] = zero4;
+      S.al[32 + lane] = zero4;
+      Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};  // partial sums since the last fold
+      int since = 0;                              // interactions per slot since the last fold
+
+      // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
+      {
+        const int nc = L.y;
+        // indices run one tile ahead of the gathers, which run one tile ahead of
+        // the arithmetic: no gather waits on the load of its own address
+        float4 ra = zero4, rb = zero4, rq0 = zero4, rq1 = zero4;
+        if (lane < nc) {
+          const size_t ci = clist[lane];
           ra = A.mom[4 * ci];
           rb = A.mom[4 * ci + 1];
           rq0 = A.mom[4 * ci + 2];
           rq1 = A.mom[4 * ci + 3];
         }
-        if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
-        __syncwarp();
-        if (k == 1) {
-#pragma unroll 1
-          for (int j = 0; j < cnt; ++j) {
-            const float4 c0 = S.sc[j][0], q0 = S.sc[j][1], q1 = S.sc[j][2];
-            pc(t0, T0, c0, q0, q1, eps2);
-            pc(t1, T1, c0, q0, q1, eps2);
+        uint32_t ci_next = (32 + lane < nc) ? clist[32 + lane] : 0u;
+        for (int base = 0; base < nc; base += 32) {
+          const int cnt = min(32, nc - base);
+          if (lane < cnt) {
+            float dx, dy, dz;
+            if (VAR == 0) {
+              dx = (ra.x - cx) + rb.x;
+              dy = (ra.y - cy) + rb.y;
+              dz = (ra.z - cz) + rb.z;
+            } else {
+              dx = ra.x;
+              dy = ra.y;
+              dz = ra.z;
+            }
+            S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
+            S.sc[lane][1] = rq0;
+            S.sc[lane][2] = make_float4(rq1.x, rq1.y, 0.f, 0.f);
+          } else {
+            S.sc[lane][0] = null_src;
+            S.sc[lane][1] = zero4;
+            S.sc[lane][2] = zero4;
           }
-        } else {
-#pragma unroll 1
-          for (int j = 0; j < cnt; j += k) {
-            pc(t0, T0, S.sc[j + ph0][0], S.sc[j + ph0][1], S.sc[j + ph0][2], eps2);
-            pc(t1, T1, S.sc[j + ph1][0], S.sc[j + ph1][1], S.sc[j + ph1][2], eps2);
+          if (base + 32 + lane < nc) {  // gather the next tile now
+            const size_t ci = ci_next;
+            ra = A.mom[4 * ci];
+            rb = A.mom[4 * ci + 1];
+            rq0 = A.mom[4 * ci + 2];
+            rq1 = A.mom[4 * ci + 3];
           }
+          if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
+          __syncwarp();
+          if (k == 1) {
+  #pragma unroll 1
+            for (int j = 0; j < cnt; ++j) {
+              const float4 c0 = S.sc[j][0], q0 = S.sc[j][1], q1 = S.sc[j][2];
+              pc(t0, T0, c0, q0, q1, eps2);
+              pc(t1, T1, c0, q0, q1, eps2);
+            }
+          } else {
+  #pragma unroll 1
+            for (int j = 0; j < cnt; j += k) {
+              pc(t0, T0, S.sc[j + ph0][0], S.sc[j + ph0][1], S.sc[j + ph0][2], eps2);
+              pc(t1, T1, S.sc[j + ph1][0], S.sc[j + ph1][1], S.sc[j + ph1][2], eps2);
+            }
+          }
+          since += (cnt + k - 1) / k;
+          if (since >= 32) {
+            fold<VAR>(S.ah[lane], S.al[lane], t0);
+            fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+            since = 0;
+          }
+          __syncwarp();
         }
-        since += (cnt + k - 1) / k;
-        if (since >= 32) {
-          fold<VAR>(S.ah[lane], S.al[lane], t0);
-          fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
-          since = 0;
-        }
-        __syncwarp();
       }
-    }
-    // ---- particle list
-    {
-      const int np = L.z;
-      float4 rh = zero4, rl = zero4;
-      int rb = -1;
-      if (lane < np) {
-        rb = (int)plist[lane];
-        rh = A.part_hi[rb];
-        rl = A.part_lo[rb];
-      }
-      int pb_next = (32 + lane < np) ? (int)plist[32 + lane] : -1;
-      for (int base = 0; base < np; base += 32) {
-        const int cnt = min(32, np - base);
-        bool member = false;
-        if (lane < cnt) {
-          member = (unsigned)(rb - gb) < (unsigned)n;
-          const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
-          S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
-          S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
-          S.pidx[lane] = rb;
-        } else {
-          S.sp[lane][0] = null_src;
-          S.sp[lane][1] = zero4;
-          S.pidx[lane] = -1;
-        }
-        if (base + 32 + lane < np) {  // gather the next tile now
-          rb = pb_next;
+      // ---- particle list
+      {
+        const int np = L.z;
+        float4 rh = zero4, rl = zero4;
+        int rb = -1;
+        if (lane < np) {
+          rb = (int)plist[lane];
           rh = A.part_hi[rb];
           rl = A.part_lo[rb];
         }
-        if (base + 64 + lane < np) pb_next = (int)plist[base + 64 + lane];
-        const bool self_tile = __any_sync(kFull, member);
-        __syncwarp();
-        if (self_tile) {
-          // a tile with the group's own bodies: skip each body's pair with itself by index
-          const int me0 = gb + b0, me1 = gb + b1;
-          for (int j = 0; j < cnt; j += k) {
-            pp<VAR, GUARD, true>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2, me0, S.pidx[j + ph0]);
-            pp<VAR, GUARD, true>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2, me1, S.pidx[j + ph1]);
+        int pb_next = (32 + lane < np) ? (int)plist[32 + lane] : -1;
+        for (int base = 0; base < np; base += 32) {
+          const int cnt = min(32, np - base);
+          bool member = false;
+          if (lane < cnt) {
+            member = (unsigned)(rb - gb) < (unsigned)n;
+            const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
+            S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
+            S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
+            S.pidx[lane] = rb;
+          } else {
+            S.sp[lane][0] = null_src;
+            S.sp[lane][1] = zero4;
+            S.pidx[lane] = -1;
           }
-        } else if (k == 1) {
-#pragma unroll 2
-          for (int j = 0; j < cnt; ++j) {
-            const float4 sh = S.sp[j][0], sl = S.sp[j][1];
-            pp<VAR, GUARD, false>(t0, T0, sh, sl, eps2);
-            pp<VAR, GUARD, false>(t1, T1, sh, sl, eps2);
+          if (base + 32 + lane < np) {  // gather the next tile now
+            rb = pb_next;
+            rh = A.part_hi[rb];
+            rl = A.part_lo[rb];
           }
-        } else {
-#pragma unroll 2
-          for (int j = 0; j < cnt; j += k) {
-            pp<VAR, GUARD, false>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2);
-            pp<VAR, GUARD, false>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2);
+          if (base + 64 + lane < np) pb_next = (int)plist[base + 64 + lane];
+          const bool self_tile = __any_sync(kFull, member);
+          __syncwarp();
+          if (self_tile) {
+            // a tile with the group's own bodies: skip each body's pair with itself by index
+            const int me0 = gb + b0, me1 = gb + b1;
+            for (int j = 0; j < cnt; j += k) {
+              pp<VAR, GUARD, true>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2, me0, S.pidx[j + ph0]);
+              pp<VAR, GUARD, true>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2, me1, S.pidx[j + ph1]);
+            }
+          } else if (k == 1) {
+  #pragma unroll 2
+            for (int j = 0; j < cnt; ++j) {
+              const float4 sh = S.sp[j][0], sl = S.sp[j][1];
+              pp<VAR, GUARD, false>(t0, T0, sh, sl, eps2);
+              pp<VAR, GUARD, false>(t1, T1, sh, sl, eps2);
+            }
+          } else {
+  #pragma unroll 2
+            for (int j = 0; j < cnt; j += k) {
+              pp<VAR, GUARD, false>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2);
+              pp<VAR, GUARD, false>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2);
+            }
           }
+          since += (cnt + k - 1) / k;
+          if (since >= 32) {
+            fold<VAR>(S.ah[lane], S.al[lane], t0);
+            fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+            since = 0;
+          }
+          __syncwarp();
         }
-        since += (cnt + k - 1) / k;
-        if (since >= 32) {
-          fold<VAR>(S.ah[lane], S.al[lane], t0);
-          fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
-          since = 0;
-        }
-        __syncwarp();
       }
-    }
-    fold<VAR>(S.ah[lane], S.al[lane], t0);
-    fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
-    __syncwarp();
+      fold<VAR>(S.ah[lane], S.al[lane], t0);
+      fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+      __syncwarp();
 
-    // ---- combine the slots of each body and write
-    auto write_body = [&](int b, float ox, float oy, float oz, float op) {
-      const int gi = gb + b;
-      if (MODE == kOutSorted) {
-        A.acc_sorted[gi] = make_float4(ox, oy, oz, op);
-      } else {
-        const size_t j = A.perm[gi];
-        A.acc_out[3 * j] = ox;
-        A.acc_out[3 * j + 1] = oy;
-        A.acc_out[3 * j + 2] = oz;
-        A.pot_out[j] = op;
-      }
-    };
-    if (k == 1) {
-      if (v0) {
-        const float4 H = S.ah[lane], Lo = S.al[lane];
-        write_body(b0, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
-      }
-      if (v1) {
-        const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
-        write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
-      }
-    } else {
-      // body b sums the compensated pairs of its slots b, b + n, ..., b + n (k - 1)
-      if (lane < n) {
-        float4 H = S.ah[lane], Lo = S.al[lane];
-        for (int q = 1; q < k; ++q) {
-          const float4 h = S.ah[lane + q * n], l = S.al[lane + q * n];
-          two_sum_into(H.x, Lo.x, h.x);
-          two_sum_into(H.y, Lo.y, h.y);
-          two_sum_into(H.z, Lo.z, h.z);
-          two_sum_into(H.w, Lo.w, h.w);
-          Lo.x += l.x;
-          Lo.y += l.y;
-          Lo.z += l.z;
-          Lo.w += l.w;
+      // ---- combine the slots of each body and write
+      auto write_body = [&](int b, float ox, float oy, float oz, float op) {
+        const int gi = gb + b;
+        if (MODE == kOutSorted) {
+          A.acc_sorted[gi] = make_float4(ox, oy, oz, op);
+        } else {
+          const size_t j = A.perm[gi];
+          A.acc_out[3 * j] = ox;
+          A.acc_out[3 * j + 1] = oy;
+          A.acc_out[3 * j + 2] = oz;
+          A.pot_out[j] = op;
         }
-        write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+      };
+      if (k == 1) {
+        if (v0) {
+          const float4 H = S.ah[lane], Lo = S.al[lane];
+          write_body(b0, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+        }
+        if (v1) {
+          const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
+          write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+        }
+      } else {
+        // body b sums the compensated pairs of its slots b, b + n, ..., b + n (k - 1)
+        if (lane < n) {
+          float4 H = S.ah[lane], Lo = S.al[lane];
+          for (int q = 1; q < k; ++q) {
+            const float4 h = S.ah[lane + q * n], l = S.al[lane + q * n];
+            two_sum_into(H.x, Lo.x, h.x);
+            two_sum_into(H.y, Lo.y, h.y);
+            two_sum_into(H.z, Lo.z, h.z);
+            two_sum_into(H.w, Lo.w, h.w);
+            Lo.x += l.x;
+            Lo.y += l.y;
+            Lo.z += l.z;
+            Lo.w += l.w;
+          }
+          write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+        }
       }
-    }
-    __syncwarp();
+      __syncwarp();
+    }  // passes
   }
 }
 
