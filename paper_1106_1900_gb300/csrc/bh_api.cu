@@ -144,9 +144,10 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.walk_stack = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.stack_capacity);
   c.list_scratch = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.list_capacity);
   c.list_pool = k.take<uint32_t>((size_t)c.pool_cap);
-  c.pool_ctr = k.take<unsigned long long>(2);
-  c.work_total = c.pool_ctr + 1;
+  c.pool_ctr = k.take<unsigned long long>(1);
   c.g_list = k.take<int4>(N);
+  c.work_hist = k.take<uint32_t>(2 * bh::kCostBuckets);
+  c.g_order = k.take<int32_t>(N);
   c.walk_queue = k.take<uint32_t>(2);
   c.d_counts = k.take<int32_t>(4);
   c.d_totals = k.take<unsigned long long>(4);

@@ -13,6 +13,7 @@ constexpr int kLevels = 20;         // 60-bit keys, 20 levels below the root (Ap
 constexpr int kRows = kLevels + 2;  // 21 cell levels + one row of group starts
 constexpr uint32_t kQMax = 1u << 20;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCostBuckets = 256;  // logarithmic buckets of a group's estimated evaluation cost
 
 // Frame of one system: origin (per-axis minimum) and power-of-two side L.
 struct __align__(32) Frame {
@@ -92,8 +93,9 @@ struct Ctx {
   int32_t *list_scratch;         // [traversal warps][2][list_capacity]
   uint32_t *list_pool;           // [pool_cap] every group's cell list then particle list
   unsigned long long *pool_ctr;  // [1]
-  unsigned long long *work_total;  // [1] estimated evaluation cost of this walk
-  int4 *g_list;                  // [G] {pool offset, cells, bodies, 0}
+  int4 *g_list;                  // [G] {pool offset, cells, bodies, estimated evaluation cost}
+  uint32_t *work_hist;           // [2][kCostBuckets] groups per cost bucket, placement counters
+  int32_t *g_order;              // [G] groups in order of decreasing estimated cost
   uint32_t *walk_queue;          // [2] traversal, evaluation
   // scalars
   int32_t *d_counts;             // [0] C, [1] G, [2] max level

@@ -180,13 +180,15 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
 // centre of mass (high part) that the walk's opening test reads.
 __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ counts, const float4 *__restrict__ mom,
                                                 float inv_theta, float4 *mac, uint32_t *queue,
-                                                unsigned long long *pool_ctr) {
+                                                unsigned long long *pool_ctr, uint32_t *work_hist) {
   const int C = counts[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the walk's group counters and list pool start empty
-    queue[0] = 0;
-    queue[1] = 0;
-    pool_ctr[0] = 0;  // list pool offset
-    pool_ctr[1] = 0;  // total estimated evaluation cost
+  if (blockIdx.x == 0) {  // the walk's group counters, list pool and cost histogram start empty
+    if (threadIdx.x == 0) {
+      queue[0] = 0;
+      queue[1] = 0;
+      pool_ctr[0] = 0;
+    }
+    for (int i = threadIdx.x; i < 2 * kCostBuckets; i += blockDim.x) work_hist[i] = 0;
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     float4 a = mom[4 * (size_t)c];
@@ -214,7 +216,7 @@ cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
 
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s) {
   float inv = (theta > 0.f) ? 1.0f / theta : INFINITY;
-  k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr);
+  k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
   c.launches++;
   return cudaGetLastError();
 }

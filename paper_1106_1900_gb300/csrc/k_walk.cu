@@ -17,15 +17,23 @@
 //              bodies to the particle list; appends are warp ballots and warp
 //              prefix sums.  The lists are written to per-warp scratch, then
 //              copied into one pool at an exact offset (one atomic per group).
-//  k_eval      one warp per group.  Lists are read 32 entries at a time; the
+//  k_order     sorts the groups by their estimated evaluation cost (a
+//              logarithmic histogram filled by k_traverse, one scatter).
+//  k_eval      one warp per group, most expensive first, so that the launch
+//              ends on cheap groups.  Lists are read 32 entries at a time; the
 //              next tile's entries are gathered into registers while the
 //              current tile (staged in shared memory) is summed.
 //
-// Slots: every lane holds two target slots, 64 per warp.  A group of n bodies
-// gets k = floor(64/n) slots per body (one for n > 32): slot s holds body
-// s mod n and takes every k-th source starting at s div n, and the slots of a
-// body are summed when the group ends -- the paper's "several threads per
-// particle" for small groups, generalised so that few slots idle.  A group of
+// Slots: every lane holds two target slots, 64 per warp.  A group of n <= 32
+// bodies is laid out with h = ceil(n/2): lane l holds bodies l mod h and
+// l mod h + h in phase l div h, so k = floor(32/h) slots per body, each taking
+// every k-th source from its phase on, summed per body when the group ends --
+// the paper's "several threads per particle" for small groups, generalised so
+// that few slots idle.  A group of n > 32 bodies has one slot per body.  Both
+// slots of a lane read the same source, so the arithmetic runs on packed FP32
+// pairs (f32x2 FMA, add, multiply: one instruction for both slots, half the
+// issue slots of scalar code at the same FP32 rate); staged values are stored
+// twice so that a 16-byte shared load yields two ready pairs.  A group of
 // 33..48 bodies would idle a quarter of the slots or more; it is evaluated in
 // two or three passes over the same lists, each for a subset of its bodies
 // small enough for three or four slots per body (eval_passes).
@@ -53,10 +61,11 @@ constexpr float kFar = 1e18f;
 constexpr int kWarps = 4;  // warps per block of both kernels
 constexpr int kThreads = 32 * kWarps;
 constexpr int kEvalMinBlocks = 6;
-
-struct Acc {
-  float x, y, z, p;
-};
+// Staging entries per warp: a 32-entry tile plus permanent nulls.  With k
+// phases a lane reads entries ph, ph + k, ... < cnt + ph, the last one at most
+// k ceil(32 / k) - 1, and k = 32 / h is one of 1, 2, 3, 4, 5, 6, 8, 10, 16,
+// 32: at most entry 39 (k = 10).
+constexpr int kStage = 40;
 
 struct Target {
   float hx, hy, hz;  // offset from the group centre, rounded
@@ -79,8 +88,11 @@ __device__ __forceinline__ float two_diff(float a, float b, float &err) {
   return s;
 }
 
-// Slots per body for a (sub)group of n <= 64 bodies on the warp's 64 slots.
-__device__ __forceinline__ int slots_per_body(int n) { return (n > 32) ? 1 : min(64 / n, 32); }
+// Slot layout of a (sub)group of n <= 64 bodies on a warp's 64 slots: lane l
+// holds bodies b = l mod h and b + h (h = pair_stride(n)) in phase l div h, so
+// both slots of a lane read the same source; a body gets 32 / h slots.
+__device__ __forceinline__ int pair_stride(int n) { return (n > 32) ? 32 : max((n + 1) >> 1, 1); }
+__device__ __forceinline__ int slots_per_body(int n) { return 32 / pair_stride(n); }
 
 // Passes over a group's lists.  A group of 33..63 bodies gets one slot per
 // body and leaves 64 - n slots idle; P passes over subsets of ceil(n / P)
@@ -104,6 +116,15 @@ __device__ __forceinline__ int eval_passes(int n) {
   }
   const int nb = (n + best - 1) / best;
   return (n + nb - 1) / nb;  // no empty last pass
+}
+
+// Logarithmic bucket of an estimated cost w >= 1: eight buckets per octave,
+// increasing with w, below kCostBuckets for any int.
+__device__ __forceinline__ int cost_bucket(int w) {
+  const unsigned u = (unsigned)max(w, 1);
+  const int msb = 31 - __clz(u);
+  const unsigned frac = (msb >= 3) ? (u >> (msb - 3)) & 7u : (u << (3 - msb)) & 7u;
+  return 8 * msb + (int)frac;
 }
 
 template <int VAR>
@@ -144,7 +165,7 @@ struct TravArgs {
   unsigned long long pool_cap;
   unsigned long long *pool_ctr;
   int4 *g_list;  // per group: {pool offset, cells, bodies, estimated evaluation cost}
-  unsigned long long *work_total;  // sum of the estimates of this launch
+  uint32_t *work_hist;  // groups per cost bucket
   int n;
   uint32_t *queue;
   int32_t *g_npc;
@@ -368,9 +389,9 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       // evaluation cost ~ (2 cells + 1 body per list entry) / slots per body
       const int P = eval_passes(n);
       const int k = slots_per_body((n + P - 1) / P);
-      const int work = P * ((2 * nc + npp + k - 1) / k + 1);
-      A.g_list[g] = full ? make_int4(0, 0, 0, 1) : make_int4((int)off, nc, npp, work);
-      atomicAdd(A.work_total, (unsigned long long)work);
+      const int work = full ? 1 : P * ((2 * nc + npp + k - 1) / k + 1);
+      A.g_list[g] = full ? make_int4(0, 0, 0, work) : make_int4((int)off, nc, npp, work);
+      atomicAdd(&A.work_hist[cost_bucket(work)], 1u);
       A.g_npc[g] = ncell;
       A.g_npp[g] = npart;
       A.g_csum[g] = csum;
@@ -385,15 +406,58 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
   }
 }
 
+// Places the groups in order of decreasing estimated cost: the groups of
+// bucket b take the slots after those of every costlier bucket (in any order
+// within the bucket; a group's result does not depend on when it is taken).
+// Every block recomputes the bucket offsets from the histogram; appends are
+// aggregated per warp over lanes of equal bucket.
+__global__ void __launch_bounds__(kCostBuckets) k_order(const int32_t *__restrict__ counts,
+                                                         const int4 *__restrict__ g_list, uint32_t *work_hist,
+                                                         int32_t *order) {
+  __shared__ uint32_t s_start[kCostBuckets];
+  __shared__ uint32_t s_warp[kCostBuckets / 32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // exclusive prefix over the buckets from the costliest down: thread t holds bucket 255 - t
+  const uint32_t v = work_hist[kCostBuckets - 1 - t];
+  uint32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  uint32_t off = 0;
+  for (int i = 0; i < w; ++i) off += s_warp[i];
+  s_start[kCostBuckets - 1 - t] = off + x - v;
+  __syncthreads();
+  const int G = counts[1];
+  uint32_t *fill = work_hist + kCostBuckets;
+  const unsigned lt = lanemask_lt();
+  for (int base = blockIdx.x * blockDim.x; base < G; base += gridDim.x * blockDim.x) {
+    const int g = base + t;
+    const int b = (g < G) ? cost_bucket(g_list[g].w) : -1;
+    const unsigned peers = __match_any_sync(kFull, b);
+    const int leader = __ffs(peers) - 1;
+    uint32_t first = 0;
+    if (lane == leader && b >= 0) first = atomicAdd(&fill[b], (uint32_t)__popc(peers));
+    first = __shfl_sync(kFull, first, leader);
+    if (b >= 0) {
+      const uint32_t pos = s_start[b] + first + (uint32_t)__popc(peers & lt);
+      if (pos < (uint32_t)G) order[pos] = g;
+    }
+  }
+}
+
 // =============================================================== evaluation
 struct EvalSmem {
-  // staged cells: (dx, dy, dz, M), (Qxx, Qyy, Qzz, Qxy), (Qxz, Qyz, 0, 0); entries >= 32 stay null
-  float4 sc[64][3];
-  // staged bodies: (S_hi, m), (S_lo, 0); entries >= 32 stay null
-  float4 sp[64][2];
-  int pidx[64];  // their sorted indices (read only for tiles holding the group's own bodies)
-  float4 ah[64];  // per slot: compensated sum (hi part) of acceleration and potential
-  float4 al[64];  // per slot: its lo part
+  // staged cells, every value twice (one per slot of a lane's pair):
+  // (dx,dx,dy,dy), (dz,dz,M,M), -(Qxx,Qxx,Qyy,Qyy), -(Qzz,Qzz,Qxy,Qxy), -(Qxz,Qxz,Qyz,Qyz)
+  float4 sc[kStage][5];
+  // staged bodies: (Sx,Sx,Sy,Sy), (Sz,Sz,m,m) of the rounded offset, (lx,lx,ly,ly), (lz,lz,0,0) of its residual
+  float4 sp[kStage][4];
+  int pidx[kStage];  // their sorted indices (read only for tiles holding the group's own bodies)
+  float4 ah[64];     // per slot: compensated sum (hi part) of acceleration and potential
+  float4 al[64];     // per slot: its lo part
 };
 
 struct EvalArgs {
@@ -404,7 +468,7 @@ struct EvalArgs {
   const int4 *__restrict__ g_list;
   const uint32_t *__restrict__ pool;
   const int32_t *__restrict__ counts;
-  const unsigned long long *__restrict__ work_total;
+  const int32_t *__restrict__ order;  // groups, most expensive first
   float eps2;
   uint32_t *queue;
   float4 *acc_sorted;
@@ -413,84 +477,118 @@ struct EvalArgs {
   const uint32_t *__restrict__ perm;
 };
 
+// The two target slots of a lane, as pairs (slot 0 in .x, slot 1 in .y).  The
+// offsets are kept negated so that a difference is one packed add.
+struct Targets2 {
+  float2 nhx, nhy, nhz;  // -(rounded offset from the group centre)
+  float2 nlx, nly, nlz;  // -(its residual)
+};
+
+// Partial sums of a lane's two slots since the last fold; the potential is
+// accumulated with the opposite sign (-phi).
+struct Acc2 {
+  float2 x, y, z, np;
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
 // Fold a slot's partial sum into its compensated (hi, lo) pair, which lives in
 // shared memory (touched once per ~32 interactions, so not worth registers).
 template <int VAR>
-__device__ __forceinline__ void fold(float4 &hs, float4 &ls, Acc &t) {
+__device__ __forceinline__ void fold(float4 &hs, float4 &ls, float x, float y, float z, float p) {
   float4 hi = hs, lo = ls;
   if (VAR == 0) {
-    two_sum_into(hi.x, lo.x, t.x);
-    two_sum_into(hi.y, lo.y, t.y);
-    two_sum_into(hi.z, lo.z, t.z);
-    two_sum_into(hi.w, lo.w, t.p);
+    two_sum_into(hi.x, lo.x, x);
+    two_sum_into(hi.y, lo.y, y);
+    two_sum_into(hi.z, lo.z, z);
+    two_sum_into(hi.w, lo.w, p);
     ls = lo;
   } else {
-    hi.x += t.x;
-    hi.y += t.y;
-    hi.z += t.z;
-    hi.w += t.p;
+    hi.x += x;
+    hi.y += y;
+    hi.z += z;
+    hi.w += p;
   }
   hs = hi;
-  t = Acc{0.f, 0.f, 0.f, 0.f};
 }
 
-// Softened particle-particle interaction of a staged source (S_hi, m), S_lo on
-// a target: 20 flops by the convention FMA = 2, rsqrt = 1 (the two-float
-// difference d = (S_hi - T_hi) + (S_lo - T_lo) costs 6 more: its first term is
-// exact for close pairs, so a pair keeps its relative accuracy however far it
-// is from the group centre).  SELF: skip the pair of a body with itself (same
-// index); GUARD: eps = 0, zero distances skipped.
+template <int VAR>
+__device__ __forceinline__ void fold2(EvalSmem &S, int lane, Acc2 &t) {
+  fold<VAR>(S.ah[lane], S.al[lane], t.x.x, t.y.x, t.z.x, -t.np.x);
+  fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t.x.y, t.y.y, t.z.y, -t.np.y);
+  const float2 z = f2(0.f, 0.f);
+  t = Acc2{z, z, z, z};
+}
+
+// Softened particle-particle interaction of one staged source with both slots
+// of a lane, in packed FP32 pairs: 20 flops per slot by the convention FMA = 2,
+// rsqrt = 1 (the two-float difference d = (S_hi - T_hi) + (S_lo - T_lo) costs 6
+// more: its first term is exact for close pairs, so a pair keeps its relative
+// accuracy however far it is from the group centre).  SELF: skip the pair of a
+// body with itself (same index); GUARD: eps = 0, zero distances skipped.
 template <int VAR, bool GUARD, bool SELF>
-__device__ __forceinline__ void pp(Acc &a, const Target &t, const float4 sh, const float4 sl, float eps2,
-                                   int me = 0, int other = 1) {
-  float dx, dy, dz;
+__device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 s0, const float4 s1, const float4 s2,
+                                    const float4 s3, float2 e2, int me0 = 0, int me1 = 0, int other = -1) {
+  float2 dx, dy, dz;
   if (VAR == 0) {
-    dx = (sh.x - t.hx) + (sl.x - t.lx);
-    dy = (sh.y - t.hy) + (sl.y - t.ly);
-    dz = (sh.z - t.hz) + (sl.z - t.lz);
+    dx = __fadd2_rn(__fadd2_rn(f2(s0.x, s0.y), t.nhx), __fadd2_rn(f2(s2.x, s2.y), t.nlx));
+    dy = __fadd2_rn(__fadd2_rn(f2(s0.z, s0.w), t.nhy), __fadd2_rn(f2(s2.z, s2.w), t.nly));
+    dz = __fadd2_rn(__fadd2_rn(f2(s1.x, s1.y), t.nhz), __fadd2_rn(f2(s3.x, s3.y), t.nlz));
   } else {
-    dx = sh.x - t.hx;
-    dy = sh.y - t.hy;
-    dz = sh.z - t.hz;
+    dx = __fadd2_rn(f2(s0.x, s0.y), t.nhx);
+    dy = __fadd2_rn(f2(s0.z, s0.w), t.nhy);
+    dz = __fadd2_rn(f2(s1.x, s1.y), t.nhz);
   }
-  float r2 = fmaf(dx, dx, eps2);
-  r2 = fmaf(dy, dy, r2);
-  r2 = fmaf(dz, dz, r2);
-  float ri = rsqrtf(r2);
-  if (GUARD) ri = (r2 > 0.f) ? ri : 0.f;
-  if (SELF) ri = (me == other) ? 0.f : ri;
-  const float mr = sh.w * ri;
-  const float mr3 = mr * ri * ri;
-  a.p -= mr;
-  a.x = fmaf(mr3, dx, a.x);
-  a.y = fmaf(mr3, dy, a.y);
-  a.z = fmaf(mr3, dz, a.z);
+  float2 r2 = __ffma2_rn(dx, dx, e2);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dz, dz, r2);
+  float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+  if (GUARD) {
+    ri.x = (r2.x > 0.f) ? ri.x : 0.f;
+    ri.y = (r2.y > 0.f) ? ri.y : 0.f;
+  }
+  if (SELF) {
+    ri.x = (me0 == other) ? 0.f : ri.x;
+    ri.y = (me1 == other) ? 0.f : ri.y;
+  }
+  const float2 mr = __fmul2_rn(f2(s1.z, s1.w), ri);
+  const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+  a.np = __fadd2_rn(a.np, mr);
+  a.x = __ffma2_rn(mr3, dx, a.x);
+  a.y = __ffma2_rn(mr3, dy, a.y);
+  a.z = __ffma2_rn(mr3, dz, a.z);
 }
 
-// Softened particle-cell interaction, monopole + quadrupole, with d = com -
-// target: a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7, phi = -M/s - (d.Q.d)/(2 s^5).
-// 54 flops by the convention above.
-__device__ __forceinline__ void pc(Acc &a, const Target &t, const float4 c0, const float4 q0, const float4 q1,
-                                   float eps2) {
-  const float dx = c0.x - t.hx, dy = c0.y - t.hy, dz = c0.z - t.hz;
-  float r2 = fmaf(dx, dx, eps2);
-  r2 = fmaf(dy, dy, r2);
-  r2 = fmaf(dz, dz, r2);
-  const float ri = rsqrtf(r2);
-  const float ri2 = ri * ri;
-  const float mr = c0.w * ri;
-  const float mr3 = mr * ri2;
-  const float qx = fmaf(q1.x, dz, fmaf(q0.w, dy, q0.x * dx));
-  const float qy = fmaf(q1.y, dz, fmaf(q0.y, dy, q0.w * dx));
-  const float qz = fmaf(q0.z, dz, fmaf(q1.y, dy, q1.x * dx));
-  const float dqd = fmaf(qz, dz, fmaf(qy, dy, qx * dx));
-  const float ri5 = ri2 * ri2 * ri;
-  const float qr5 = dqd * ri5;
-  a.p = fmaf(-0.5f, qr5, a.p - mr);
-  const float coef = fmaf(2.5f * qr5, ri2, mr3);
-  a.x = fmaf(-ri5, qx, fmaf(coef, dx, a.x));
-  a.y = fmaf(-ri5, qy, fmaf(coef, dy, a.y));
-  a.z = fmaf(-ri5, qz, fmaf(coef, dz, a.z));
+// Softened particle-cell interaction, monopole + quadrupole, of one staged cell
+// with both slots of a lane, with d = com - target:
+//   a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7,  phi = -M/s - (d.Q.d)/(2 s^5).
+// 54 flops per slot by the convention above.  The staged Q is negated, so
+// q = -Q d and w = -d.Q.d come out of plain products.
+__device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0, const float4 c1, const float4 c2,
+                                    const float4 c3, const float4 c4, float2 e2) {
+  const float2 dx = __fadd2_rn(f2(c0.x, c0.y), t.nhx);
+  const float2 dy = __fadd2_rn(f2(c0.z, c0.w), t.nhy);
+  const float2 dz = __fadd2_rn(f2(c1.x, c1.y), t.nhz);
+  float2 r2 = __ffma2_rn(dx, dx, e2);
+  r2 = __ffma2_rn(dy, dy, r2);
+  r2 = __ffma2_rn(dz, dz, r2);
+  const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+  const float2 ri2 = __fmul2_rn(ri, ri);
+  const float2 mr = __fmul2_rn(f2(c1.z, c1.w), ri);
+  const float2 mr3 = __fmul2_rn(mr, ri2);
+  const float2 qxx = f2(c2.x, c2.y), qyy = f2(c2.z, c2.w), qzz = f2(c3.x, c3.y);
+  const float2 qxy = f2(c3.z, c3.w), qxz = f2(c4.x, c4.y), qyz = f2(c4.z, c4.w);
+  const float2 qx = __ffma2_rn(qxz, dz, __ffma2_rn(qxy, dy, __fmul2_rn(qxx, dx)));
+  const float2 qy = __ffma2_rn(qyz, dz, __ffma2_rn(qyy, dy, __fmul2_rn(qxy, dx)));
+  const float2 qz = __ffma2_rn(qzz, dz, __ffma2_rn(qyz, dy, __fmul2_rn(qxz, dx)));
+  const float2 w = __ffma2_rn(qz, dz, __ffma2_rn(qy, dy, __fmul2_rn(qx, dx)));
+  const float2 ri5 = __fmul2_rn(__fmul2_rn(ri2, ri2), ri);
+  const float2 w5 = __fmul2_rn(w, ri5);
+  a.np = __ffma2_rn(f2(-0.5f, -0.5f), w5, __fadd2_rn(a.np, mr));
+  const float2 coef = __ffma2_rn(__fmul2_rn(f2(-2.5f, -2.5f), w5), ri2, mr3);
+  a.x = __ffma2_rn(qx, ri5, __ffma2_rn(coef, dx, a.x));
+  a.y = __ffma2_rn(qy, ri5, __ffma2_rn(coef, dy, a.y));
+  a.z = __ffma2_rn(qz, ri5, __ffma2_rn(coef, dz, a.z));
 }
 
 template <int VAR, bool GUARD, int MODE>
@@ -498,31 +596,34 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
   extern __shared__ EvalSmem s_eval[];
   const int lane = threadIdx.x & 31;
   EvalSmem &S = s_eval[threadIdx.x >> 5];
-  const float eps2 = A.eps2;
-  const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);
+  const float2 e2 = f2(A.eps2, A.eps2);
+  const float4 null_pos = make_float4(kFar, kFar, kFar, kFar);  // far away, zero mass, no quadrupole
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  // entries 32..63 of the staging arrays are permanent nulls (zero mass, far away)
-  S.sc[32 + lane][0] = null_src;
-  S.sc[32 + lane][1] = zero4;
-  S.sc[32 + lane][2] = zero4;
-  S.sp[32 + lane][0] = null_src;
-  S.sp[32 + lane][1] = zero4;
-  S.pidx[32 + lane] = -1;
+  const float4 null_mass = make_float4(kFar, kFar, 0.f, 0.f);
+  // entries 32..kStage-1 of the staging arrays are permanent nulls
+  if (lane < kStage - 32) {
+    S.sc[32 + lane][0] = null_pos;
+    S.sc[32 + lane][1] = null_mass;
+    S.sc[32 + lane][2] = zero4;
+    S.sc[32 + lane][3] = zero4;
+    S.sc[32 + lane][4] = zero4;
+    S.sp[32 + lane][0] = null_pos;
+    S.sp[32 + lane][1] = null_mass;
+    S.sp[32 + lane][2] = zero4;
+    S.sp[32 + lane][3] = zero4;
+    S.pidx[32 + lane] = -1;
+  }
   __syncwarp();
   const int G = A.counts[1];
-  // longest first, coarsely: one sweep over the groups for those that cost more
-  // than twice the mean, then one for the rest, so that the launch does not end
-  // waiting on a few expensive groups taken last
-  const unsigned long long heavy = 2 * (*A.work_total) / (unsigned long long)max(G, 1);
-
+  // groups are taken most expensive first, so that the launch ends on cheap ones
   while (true) {
     int q = 0;
     if (lane == 0) q = (int)atomicAdd(A.queue, 1u);
     q = __shfl_sync(kFull, q, 0);
-    if (q >= 2 * G) break;
-    const int g = (q < G) ? q : q - G;
+    if (q >= G) break;
+    const int g = A.order[q];
+    if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
     const int4 L = A.g_list[g];
-    if ((q < G) != ((unsigned long long)L.w > heavy)) continue;
     const int gb0 = A.g_beg[g];
     const int ng = A.g_beg[g + 1] - gb0;
     float cx = 0.f, cy = 0.f, cz = 0.f;
@@ -538,35 +639,33 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
       // this pass: bodies gb .. gb + n - 1 of the group, on the group's lists
       const int gb = gb0 + pass * nbp;
       const int n = min(nbp, ng - pass * nbp);
-      const int k = slots_per_body(n);
       const uint32_t *clist = A.pool + (unsigned)L.x;
       const uint32_t *plist = clist + L.y;
-      int b0, b1, ph0, ph1;
-      bool v0, v1;
-      if (k == 1) {
-        b0 = lane;
-        b1 = lane + 32;
-        ph0 = ph1 = 0;
-        v0 = b0 < n;
-        v1 = b1 < n;
-      } else {
-        const int ns = n * k;
-        v0 = lane < ns;
-        v1 = lane + 32 < ns;
-        b0 = lane % n;
-        b1 = (lane + 32) % n;
-        ph0 = v0 ? lane / n : 0;
-        ph1 = v1 ? (lane + 32) / n : 0;
+      // lane -> (phase ph, bodies b0 and b1 = b0 + h): both slots read the same entry
+      const int h = pair_stride(n);
+      const int k = 32 / h;  // phases = slots per body
+      const int ph = min(lane / h, k - 1);
+      const int b0 = lane % h, b1 = b0 + h;
+      const bool v0 = lane < h * k && b0 < n, v1 = lane < h * k && b1 < n;
+      Targets2 T;
+      {
+        const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
+        const Target t0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
+        const Target t1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
+        T.nhx = f2(-t0.hx, -t1.hx);
+        T.nhy = f2(-t0.hy, -t1.hy);
+        T.nhz = f2(-t0.hz, -t1.hz);
+        T.nlx = f2(-t0.lx, -t1.lx);
+        T.nly = f2(-t0.ly, -t1.ly);
+        T.nlz = f2(-t0.lz, -t1.lz);
       }
-      const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
-      const Target T0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
-      const Target T1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
       S.ah[lane] = zero4;
       S.al[lane] = zero4;
       S.ah[32 + lane] = zero4;
       S.al[32 + lane] = zero4;
-      Acc t0 = {0, 0, 0, 0}, t1 = {0, 0, 0, 0};  // partial sums since the last fold
-      int since = 0;                              // interactions per slot since the last fold
+      Acc2 t;  // partial sums since the last fold
+      t.x = t.y = t.z = t.np = f2(0.f, 0.f);
+      int since = 0;  // interactions per slot since the last fold
 
       // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
       {
@@ -595,13 +694,17 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
               dy = ra.y;
               dz = ra.z;
             }
-            S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
-            S.sc[lane][1] = rq0;
-            S.sc[lane][2] = make_float4(rq1.x, rq1.y, 0.f, 0.f);
+            S.sc[lane][0] = make_float4(dx, dx, dy, dy);
+            S.sc[lane][1] = make_float4(dz, dz, ra.w, ra.w);
+            S.sc[lane][2] = make_float4(-rq0.x, -rq0.x, -rq0.y, -rq0.y);
+            S.sc[lane][3] = make_float4(-rq0.z, -rq0.z, -rq0.w, -rq0.w);
+            S.sc[lane][4] = make_float4(-rq1.x, -rq1.x, -rq1.y, -rq1.y);
           } else {
-            S.sc[lane][0] = null_src;
-            S.sc[lane][1] = zero4;
+            S.sc[lane][0] = null_pos;
+            S.sc[lane][1] = null_mass;
             S.sc[lane][2] = zero4;
+            S.sc[lane][3] = zero4;
+            S.sc[lane][4] = zero4;
           }
           if (base + 32 + lane < nc) {  // gather the next tile now
             const size_t ci = ci_next;
@@ -612,24 +715,14 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
           }
           if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
           __syncwarp();
-          if (k == 1) {
-  #pragma unroll 1
-            for (int j = 0; j < cnt; ++j) {
-              const float4 c0 = S.sc[j][0], q0 = S.sc[j][1], q1 = S.sc[j][2];
-              pc(t0, T0, c0, q0, q1, eps2);
-              pc(t1, T1, c0, q0, q1, eps2);
-            }
-          } else {
-  #pragma unroll 1
-            for (int j = 0; j < cnt; j += k) {
-              pc(t0, T0, S.sc[j + ph0][0], S.sc[j + ph0][1], S.sc[j + ph0][2], eps2);
-              pc(t1, T1, S.sc[j + ph1][0], S.sc[j + ph1][1], S.sc[j + ph1][2], eps2);
-            }
+#pragma unroll 1
+          for (int j = ph; j < cnt + ph; j += k) {
+            const float4 *e = S.sc[j];
+            pc2(t, T, e[0], e[1], e[2], e[3], e[4], e2);
           }
           since += (cnt + k - 1) / k;
           if (since >= 32) {
-            fold<VAR>(S.ah[lane], S.al[lane], t0);
-            fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+            fold2<VAR>(S, lane, t);
             since = 0;
           }
           __syncwarp();
@@ -652,12 +745,16 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
           if (lane < cnt) {
             member = (unsigned)(rb - gb) < (unsigned)n;
             const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
-            S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
-            S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
+            S.sp[lane][0] = make_float4(s.hx, s.hx, s.hy, s.hy);
+            S.sp[lane][1] = make_float4(s.hz, s.hz, rh.w, rh.w);
+            S.sp[lane][2] = make_float4(s.lx, s.lx, s.ly, s.ly);
+            S.sp[lane][3] = make_float4(s.lz, s.lz, 0.f, 0.f);
             S.pidx[lane] = rb;
           } else {
-            S.sp[lane][0] = null_src;
-            S.sp[lane][1] = zero4;
+            S.sp[lane][0] = null_pos;
+            S.sp[lane][1] = null_mass;
+            S.sp[lane][2] = zero4;
+            S.sp[lane][3] = zero4;
             S.pidx[lane] = -1;
           }
           if (base + 32 + lane < np) {  // gather the next tile now
@@ -671,35 +768,26 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
           if (self_tile) {
             // a tile with the group's own bodies: skip each body's pair with itself by index
             const int me0 = gb + b0, me1 = gb + b1;
-            for (int j = 0; j < cnt; j += k) {
-              pp<VAR, GUARD, true>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2, me0, S.pidx[j + ph0]);
-              pp<VAR, GUARD, true>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2, me1, S.pidx[j + ph1]);
-            }
-          } else if (k == 1) {
-  #pragma unroll 2
-            for (int j = 0; j < cnt; ++j) {
-              const float4 sh = S.sp[j][0], sl = S.sp[j][1];
-              pp<VAR, GUARD, false>(t0, T0, sh, sl, eps2);
-              pp<VAR, GUARD, false>(t1, T1, sh, sl, eps2);
+            for (int j = ph; j < cnt + ph; j += k) {
+              const float4 *e = S.sp[j];
+              pp2<VAR, GUARD, true>(t, T, e[0], e[1], e[2], e[3], e2, me0, me1, S.pidx[j]);
             }
           } else {
-  #pragma unroll 2
-            for (int j = 0; j < cnt; j += k) {
-              pp<VAR, GUARD, false>(t0, T0, S.sp[j + ph0][0], S.sp[j + ph0][1], eps2);
-              pp<VAR, GUARD, false>(t1, T1, S.sp[j + ph1][0], S.sp[j + ph1][1], eps2);
+#pragma unroll 2
+            for (int j = ph; j < cnt + ph; j += k) {
+              const float4 *e = S.sp[j];
+              pp2<VAR, GUARD, false>(t, T, e[0], e[1], e[2], e[3], e2);
             }
           }
           since += (cnt + k - 1) / k;
           if (since >= 32) {
-            fold<VAR>(S.ah[lane], S.al[lane], t0);
-            fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+            fold2<VAR>(S, lane, t);
             since = 0;
           }
           __syncwarp();
         }
       }
-      fold<VAR>(S.ah[lane], S.al[lane], t0);
-      fold<VAR>(S.ah[32 + lane], S.al[32 + lane], t1);
+      fold2<VAR>(S, lane, t);
       __syncwarp();
 
       // ---- combine the slots of each body and write
@@ -724,23 +812,23 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
           const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
           write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
         }
-      } else {
-        // body b sums the compensated pairs of its slots b, b + n, ..., b + n (k - 1)
-        if (lane < n) {
-          float4 H = S.ah[lane], Lo = S.al[lane];
-          for (int q = 1; q < k; ++q) {
-            const float4 h = S.ah[lane + q * n], l = S.al[lane + q * n];
-            two_sum_into(H.x, Lo.x, h.x);
-            two_sum_into(H.y, Lo.y, h.y);
-            two_sum_into(H.z, Lo.z, h.z);
-            two_sum_into(H.w, Lo.w, h.w);
-            Lo.x += l.x;
-            Lo.y += l.y;
-            Lo.z += l.z;
-            Lo.w += l.w;
-          }
-          write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+      } else if (lane < n) {
+        // body b's slots: b + q h (q < k) in the first half of the slot array
+        // for b < h, b - h + q h in the second half otherwise
+        const int s0 = (lane < h) ? lane : 32 + lane - h;
+        float4 H = S.ah[s0], Lo = S.al[s0];
+        for (int q = 1; q < k; ++q) {
+          const float4 hq = S.ah[s0 + q * h], lq = S.al[s0 + q * h];
+          two_sum_into(H.x, Lo.x, hq.x);
+          two_sum_into(H.y, Lo.y, hq.y);
+          two_sum_into(H.z, Lo.z, hq.z);
+          two_sum_into(H.w, Lo.w, hq.w);
+          Lo.x += lq.x;
+          Lo.y += lq.y;
+          Lo.z += lq.z;
+          Lo.w += lq.w;
         }
+        write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
       }
       __syncwarp();
     }  // passes
@@ -877,7 +965,7 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   t.pool_cap = (unsigned long long)c.pool_cap;
   t.pool_ctr = c.pool_ctr;
   t.g_list = c.g_list;
-  t.work_total = c.work_total;
+  t.work_hist = c.work_hist;
   t.n = (int)c.n;
   t.queue = c.walk_queue;
   t.g_npc = c.g_npc;
@@ -892,6 +980,10 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   cudaError_t e = cudaGetLastError();
   c.launches++;
   if (e) return e;
+  k_order<<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.work_hist, c.g_order);
+  e = cudaGetLastError();
+  c.launches++;
+  if (e) return e;
   if (c.profiling) {
     if (c.capturing) cudaEventRecordWithFlags(c.ev[8][0], s, cudaEventRecordExternal);
     else cudaEventRecord(c.ev[8][0], s);
@@ -904,7 +996,7 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   a.g_list = c.g_list;
   a.pool = c.list_pool;
   a.counts = c.d_counts;
-  a.work_total = c.work_total;
+  a.order = c.g_order;
   a.eps2 = eps * eps;
   a.queue = c.walk_queue + 1;
   a.acc_sorted = c.acc_sorted;
