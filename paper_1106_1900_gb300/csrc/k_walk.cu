@@ -32,8 +32,8 @@
 // that few slots idle.  A group of n > 32 bodies has one slot per body.  Both
 // slots of a lane read the same source, so the arithmetic runs on packed FP32
 // pairs (f32x2 FMA, add, multiply: one instruction for both slots, half the
-// issue slots of scalar code at the same FP32 rate); staged values are stored
-// twice so that a 16-byte shared load yields two ready pairs.  A group of
+// issue slots of scalar code at the same FP32 rate); a staged value is read
+// once and paired with itself in registers.  A group of
 // 33..48 bodies would idle a quarter of the slots or more; it is evaluated in
 // two or three passes over the same lists, each for a subset of its bodies
 // small enough for three or four slots per body (eval_passes).
@@ -450,11 +450,10 @@ __global__ void __launch_bounds__(kCostBuckets) k_order(const int32_t *__restric
 
 // =============================================================== evaluation
 struct EvalSmem {
-  // staged cells, every value twice (one per slot of a lane's pair):
-  // (dx,dx,dy,dy), (dz,dz,M,M), -(Qxx,Qxx,Qyy,Qyy), -(Qzz,Qzz,Qxy,Qxy), -(Qxz,Qxz,Qyz,Qyz)
-  float4 sc[kStage][5];
-  // staged bodies: (Sx,Sx,Sy,Sy), (Sz,Sz,m,m) of the rounded offset, (lx,lx,ly,ly), (lz,lz,0,0) of its residual
-  float4 sp[kStage][4];
+  // staged cells: (dx, dy, dz, M), -(Qxx, Qyy, Qzz, Qxy), -(Qxz, Qyz, 0, 0)
+  float4 sc[kStage][3];
+  // staged bodies: (S_hi, m), (S_lo, 0) -- the rounded offset and its residual
+  float4 sp[kStage][2];
   int pidx[kStage];  // their sorted indices (read only for tiles holding the group's own bodies)
   float4 ah[64];     // per slot: compensated sum (hi part) of acceleration and potential
   float4 al[64];     // per slot: its lo part
@@ -527,17 +526,17 @@ __device__ __forceinline__ void fold2(EvalSmem &S, int lane, Acc2 &t) {
 // accuracy however far it is from the group centre).  SELF: skip the pair of a
 // body with itself (same index); GUARD: eps = 0, zero distances skipped.
 template <int VAR, bool GUARD, bool SELF>
-__device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 s0, const float4 s1, const float4 s2,
-                                    const float4 s3, float2 e2, int me0 = 0, int me1 = 0, int other = -1) {
+__device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 sh, const float4 sl, float2 e2,
+                                    int me0 = 0, int me1 = 0, int other = -1) {
   float2 dx, dy, dz;
   if (VAR == 0) {
-    dx = __fadd2_rn(__fadd2_rn(f2(s0.x, s0.y), t.nhx), __fadd2_rn(f2(s2.x, s2.y), t.nlx));
-    dy = __fadd2_rn(__fadd2_rn(f2(s0.z, s0.w), t.nhy), __fadd2_rn(f2(s2.z, s2.w), t.nly));
-    dz = __fadd2_rn(__fadd2_rn(f2(s1.x, s1.y), t.nhz), __fadd2_rn(f2(s3.x, s3.y), t.nlz));
+    dx = __fadd2_rn(__fadd2_rn(f2(sh.x, sh.x), t.nhx), __fadd2_rn(f2(sl.x, sl.x), t.nlx));
+    dy = __fadd2_rn(__fadd2_rn(f2(sh.y, sh.y), t.nhy), __fadd2_rn(f2(sl.y, sl.y), t.nly));
+    dz = __fadd2_rn(__fadd2_rn(f2(sh.z, sh.z), t.nhz), __fadd2_rn(f2(sl.z, sl.z), t.nlz));
   } else {
-    dx = __fadd2_rn(f2(s0.x, s0.y), t.nhx);
-    dy = __fadd2_rn(f2(s0.z, s0.w), t.nhy);
-    dz = __fadd2_rn(f2(s1.x, s1.y), t.nhz);
+    dx = __fadd2_rn(f2(sh.x, sh.x), t.nhx);
+    dy = __fadd2_rn(f2(sh.y, sh.y), t.nhy);
+    dz = __fadd2_rn(f2(sh.z, sh.z), t.nhz);
   }
   float2 r2 = __ffma2_rn(dx, dx, e2);
   r2 = __ffma2_rn(dy, dy, r2);
@@ -551,7 +550,7 @@ __device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 s0,
     ri.x = (me0 == other) ? 0.f : ri.x;
     ri.y = (me1 == other) ? 0.f : ri.y;
   }
-  const float2 mr = __fmul2_rn(f2(s1.z, s1.w), ri);
+  const float2 mr = __fmul2_rn(f2(sh.w, sh.w), ri);
   const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
   a.np = __fadd2_rn(a.np, mr);
   a.x = __ffma2_rn(mr3, dx, a.x);
@@ -564,20 +563,20 @@ __device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 s0,
 //   a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7,  phi = -M/s - (d.Q.d)/(2 s^5).
 // 54 flops per slot by the convention above.  The staged Q is negated, so
 // q = -Q d and w = -d.Q.d come out of plain products.
-__device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0, const float4 c1, const float4 c2,
-                                    const float4 c3, const float4 c4, float2 e2) {
-  const float2 dx = __fadd2_rn(f2(c0.x, c0.y), t.nhx);
-  const float2 dy = __fadd2_rn(f2(c0.z, c0.w), t.nhy);
-  const float2 dz = __fadd2_rn(f2(c1.x, c1.y), t.nhz);
+__device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0, const float4 q0, const float4 q1,
+                                    float2 e2) {
+  const float2 dx = __fadd2_rn(f2(c0.x, c0.x), t.nhx);
+  const float2 dy = __fadd2_rn(f2(c0.y, c0.y), t.nhy);
+  const float2 dz = __fadd2_rn(f2(c0.z, c0.z), t.nhz);
   float2 r2 = __ffma2_rn(dx, dx, e2);
   r2 = __ffma2_rn(dy, dy, r2);
   r2 = __ffma2_rn(dz, dz, r2);
   const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
   const float2 ri2 = __fmul2_rn(ri, ri);
-  const float2 mr = __fmul2_rn(f2(c1.z, c1.w), ri);
+  const float2 mr = __fmul2_rn(f2(c0.w, c0.w), ri);
   const float2 mr3 = __fmul2_rn(mr, ri2);
-  const float2 qxx = f2(c2.x, c2.y), qyy = f2(c2.z, c2.w), qzz = f2(c3.x, c3.y);
-  const float2 qxy = f2(c3.z, c3.w), qxz = f2(c4.x, c4.y), qyz = f2(c4.z, c4.w);
+  const float2 qxx = f2(q0.x, q0.x), qyy = f2(q0.y, q0.y), qzz = f2(q0.z, q0.z);
+  const float2 qxy = f2(q0.w, q0.w), qxz = f2(q1.x, q1.x), qyz = f2(q1.y, q1.y);
   const float2 qx = __ffma2_rn(qxz, dz, __ffma2_rn(qxy, dy, __fmul2_rn(qxx, dx)));
   const float2 qy = __ffma2_rn(qyz, dz, __ffma2_rn(qyy, dy, __fmul2_rn(qxy, dx)));
   const float2 qz = __ffma2_rn(qzz, dz, __ffma2_rn(qyz, dy, __fmul2_rn(qxz, dx)));
@@ -597,20 +596,15 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
   const int lane = threadIdx.x & 31;
   EvalSmem &S = s_eval[threadIdx.x >> 5];
   const float2 e2 = f2(A.eps2, A.eps2);
-  const float4 null_pos = make_float4(kFar, kFar, kFar, kFar);  // far away, zero mass, no quadrupole
+  const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);  // far away, zero mass, no quadrupole
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 null_mass = make_float4(kFar, kFar, 0.f, 0.f);
   // entries 32..kStage-1 of the staging arrays are permanent nulls
   if (lane < kStage - 32) {
-    S.sc[32 + lane][0] = null_pos;
-    S.sc[32 + lane][1] = null_mass;
+    S.sc[32 + lane][0] = null_src;
+    S.sc[32 + lane][1] = zero4;
     S.sc[32 + lane][2] = zero4;
-    S.sc[32 + lane][3] = zero4;
-    S.sc[32 + lane][4] = zero4;
-    S.sp[32 + lane][0] = null_pos;
-    S.sp[32 + lane][1] = null_mass;
-    S.sp[32 + lane][2] = zero4;
-    S.sp[32 + lane][3] = zero4;
+    S.sp[32 + lane][0] = null_src;
+    S.sp[32 + lane][1] = zero4;
     S.pidx[32 + lane] = -1;
   }
   __syncwarp();
@@ -694,17 +688,13 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
               dy = ra.y;
               dz = ra.z;
             }
-            S.sc[lane][0] = make_float4(dx, dx, dy, dy);
-            S.sc[lane][1] = make_float4(dz, dz, ra.w, ra.w);
-            S.sc[lane][2] = make_float4(-rq0.x, -rq0.x, -rq0.y, -rq0.y);
-            S.sc[lane][3] = make_float4(-rq0.z, -rq0.z, -rq0.w, -rq0.w);
-            S.sc[lane][4] = make_float4(-rq1.x, -rq1.x, -rq1.y, -rq1.y);
+            S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
+            S.sc[lane][1] = make_float4(-rq0.x, -rq0.y, -rq0.z, -rq0.w);
+            S.sc[lane][2] = make_float4(-rq1.x, -rq1.y, 0.f, 0.f);
           } else {
-            S.sc[lane][0] = null_pos;
-            S.sc[lane][1] = null_mass;
+            S.sc[lane][0] = null_src;
+            S.sc[lane][1] = zero4;
             S.sc[lane][2] = zero4;
-            S.sc[lane][3] = zero4;
-            S.sc[lane][4] = zero4;
           }
           if (base + 32 + lane < nc) {  // gather the next tile now
             const size_t ci = ci_next;
@@ -718,7 +708,7 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
 #pragma unroll 1
           for (int j = ph; j < cnt + ph; j += k) {
             const float4 *e = S.sc[j];
-            pc2(t, T, e[0], e[1], e[2], e[3], e[4], e2);
+            pc2(t, T, e[0], e[1], e[2], e2);
           }
           since += (cnt + k - 1) / k;
           if (since >= 32) {
@@ -745,16 +735,12 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
           if (lane < cnt) {
             member = (unsigned)(rb - gb) < (unsigned)n;
             const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
-            S.sp[lane][0] = make_float4(s.hx, s.hx, s.hy, s.hy);
-            S.sp[lane][1] = make_float4(s.hz, s.hz, rh.w, rh.w);
-            S.sp[lane][2] = make_float4(s.lx, s.lx, s.ly, s.ly);
-            S.sp[lane][3] = make_float4(s.lz, s.lz, 0.f, 0.f);
+            S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
+            S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
             S.pidx[lane] = rb;
           } else {
-            S.sp[lane][0] = null_pos;
-            S.sp[lane][1] = null_mass;
-            S.sp[lane][2] = zero4;
-            S.sp[lane][3] = zero4;
+            S.sp[lane][0] = null_src;
+            S.sp[lane][1] = zero4;
             S.pidx[lane] = -1;
           }
           if (base + 32 + lane < np) {  // gather the next tile now
@@ -770,13 +756,13 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
             const int me0 = gb + b0, me1 = gb + b1;
             for (int j = ph; j < cnt + ph; j += k) {
               const float4 *e = S.sp[j];
-              pp2<VAR, GUARD, true>(t, T, e[0], e[1], e[2], e[3], e2, me0, me1, S.pidx[j]);
+              pp2<VAR, GUARD, true>(t, T, e[0], e[1], e2, me0, me1, S.pidx[j]);
             }
           } else {
 #pragma unroll 2
             for (int j = ph; j < cnt + ph; j += k) {
               const float4 *e = S.sp[j];
-              pp2<VAR, GUARD, false>(t, T, e[0], e[1], e[2], e[3], e2);
+              pp2<VAR, GUARD, false>(t, T, e[0], e[1], e2);
             }
           }
           since += (cnt + k - 1) / k;
