@@ -28,9 +28,13 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ unsigned long long ord_of(double x) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+// Order-preserving image of a double's bits as an unsigned integer (any
+// non-NaN: x < y iff ord(x) < ord(y); -0 sorts just below +0).
+__device__ __forceinline__ unsigned long long ord_bits(unsigned long long b) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ bool finite_bits(unsigned long long b) {
+  return ((b >> 52) & 0x7ffull) != 0x7ffull;
 }
 __device__ __forceinline__ double double_of(unsigned long long o) {
   unsigned long long b = (o >> 63) ? (o & 0x7fffffffffffffffull) : ~o;
@@ -53,44 +57,47 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
                                                  int n, const int32_t *__restrict__ offs, int S,
                                                  unsigned long long *minmax, uint32_t *ticket, Frame *frame,
                                                  int32_t *status) {
-  __shared__ double s_v[kBlock / 32][6];
+  __shared__ unsigned long long s_v[kBlock / 32][6];
   __shared__ int s_sys[kBlock / 32];
   __shared__ bool s_last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int base = blockIdx.x * (4 * kBlock);
-  double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  // min/max on the order-preserving integer images of the coordinates: exact,
+  // and integer work (the GPU's FP64 rate is a small fraction of its FP32 rate)
+  unsigned long long v[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
   int my_sys = -1;
-  bool bad = false, mixed = false;
+  bool bad = false;
   for (int j = 0; j < 4; ++j) {
     int i = base + threadIdx.x + j * kBlock;
     if (i >= n) break;
-    double x0 = pos[3 * (size_t)i], x1 = pos[3 * (size_t)i + 1], x2 = pos[3 * (size_t)i + 2];
-    double m = mass[i];
-    bad |= !(isfinite(x0) && isfinite(x1) && isfinite(x2) && isfinite(m));
+    const unsigned long long x0 = (unsigned long long)__double_as_longlong(pos[3 * (size_t)i]);
+    const unsigned long long x1 = (unsigned long long)__double_as_longlong(pos[3 * (size_t)i + 1]);
+    const unsigned long long x2 = (unsigned long long)__double_as_longlong(pos[3 * (size_t)i + 2]);
+    const unsigned long long m = (unsigned long long)__double_as_longlong(mass[i]);
+    bad |= !(finite_bits(x0) && finite_bits(x1) && finite_bits(x2) && finite_bits(m));
     int s = FOREST ? sys_of(offs, S, i) : 0;
     if (my_sys >= 0 && s != my_sys) {
       // body of another system: flush what we have and start again
       for (int a = 0; a < 3; ++a) {
-        atomicMin(&minmax[6 * my_sys + a], ord_of(v[a]));
-        atomicMax(&minmax[6 * my_sys + 3 + a], ord_of(v[3 + a]));
+        atomicMin(&minmax[6 * my_sys + a], v[a]);
+        atomicMax(&minmax[6 * my_sys + 3 + a], v[3 + a]);
       }
-      v[0] = v[1] = v[2] = INFINITY;
-      v[3] = v[4] = v[5] = -INFINITY;
-      mixed = true;
+      v[0] = v[1] = v[2] = ~0ull;
+      v[3] = v[4] = v[5] = 0ull;
     }
     my_sys = s;
-    v[0] = fmin(v[0], x0); v[1] = fmin(v[1], x1); v[2] = fmin(v[2], x2);
-    v[3] = fmax(v[3], x0); v[4] = fmax(v[4], x1); v[5] = fmax(v[5], x2);
+    const unsigned long long o0 = ord_bits(x0), o1 = ord_bits(x1), o2 = ord_bits(x2);
+    v[0] = min(v[0], o0); v[1] = min(v[1], o1); v[2] = min(v[2], o2);
+    v[3] = max(v[3], o0); v[4] = max(v[4], o1); v[5] = max(v[5], o2);
   }
-  (void)mixed;
   if (bad) set_status(status, BH_ERR_NONFINITE);
   int s0 = __shfl_sync(kFull, my_sys, 0);
   bool uniform = __all_sync(kFull, my_sys == s0 || my_sys < 0) && s0 >= 0;
   if (uniform) {
     for (int o = 16; o > 0; o >>= 1)
       for (int a = 0; a < 3; ++a) {
-        v[a] = fmin(v[a], __shfl_xor_sync(kFull, v[a], o));
-        v[3 + a] = fmax(v[3 + a], __shfl_xor_sync(kFull, v[3 + a], o));
+        v[a] = min(v[a], __shfl_xor_sync(kFull, v[a], o));
+        v[3 + a] = max(v[3 + a], __shfl_xor_sync(kFull, v[3 + a], o));
       }
     if (lane == 0) {
       for (int a = 0; a < 6; ++a) s_v[warp][a] = v[a];
@@ -99,8 +106,8 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
   } else {
     if (my_sys >= 0)
       for (int a = 0; a < 3; ++a) {
-        atomicMin(&minmax[6 * my_sys + a], ord_of(v[a]));
-        atomicMax(&minmax[6 * my_sys + 3 + a], ord_of(v[3 + a]));
+        atomicMin(&minmax[6 * my_sys + a], v[a]);
+        atomicMax(&minmax[6 * my_sys + 3 + a], v[3 + a]);
       }
     if (lane == 0) s_sys[warp] = -1;
   }
@@ -108,13 +115,13 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
   if (threadIdx.x == 0) {
     // merge the warps' partials, one set of atomics per run of equal systems
     int cur = -1;
-    double acc[6];
+    unsigned long long acc[6];
     for (int w = 0; w <= kBlock / 32; ++w) {
       int s = (w < kBlock / 32) ? s_sys[w] : -2;
       if (s != cur && cur >= 0) {
         for (int a = 0; a < 3; ++a) {
-          atomicMin(&minmax[6 * cur + a], ord_of(acc[a]));
-          atomicMax(&minmax[6 * cur + 3 + a], ord_of(acc[3 + a]));
+          atomicMin(&minmax[6 * cur + a], acc[a]);
+          atomicMax(&minmax[6 * cur + 3 + a], acc[3 + a]);
         }
         cur = -1;
       }
@@ -124,8 +131,8 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
           for (int a = 0; a < 6; ++a) acc[a] = s_v[w][a];
         } else {
           for (int a = 0; a < 3; ++a) {
-            acc[a] = fmin(acc[a], s_v[w][a]);
-            acc[3 + a] = fmax(acc[3 + a], s_v[w][3 + a]);
+            acc[a] = min(acc[a], s_v[w][a]);
+            acc[3 + a] = max(acc[3 + a], s_v[w][3 + a]);
           }
         }
       }
@@ -161,6 +168,24 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
 }
 
 // ----------------------------------------------------------------- keys
+// floor(d * 2^k) clamped to [0, 2^20 - 1], from the bits of d: a product with a
+// power of two is exact (or, below 2^-1022, under 1 anyway), so this equals
+// clamp(floor(__dmul_rn(d, 2^k))) without FP64 arithmetic.  NaN gives 0.
+__device__ __forceinline__ uint32_t quantize(double d, int k) {
+  const long long b = __double_as_longlong(d);
+  if (b <= 0) return 0;  // negative, -0 or +0
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long frac = (unsigned long long)b & ((1ull << 52) - 1);
+  if (e == 0x7ff) return frac ? 0u : kQMax - 1;  // NaN, +inf
+  // d = m 2^(e' - 1075) with the hidden bit (normal) or e' = 1 (subnormal)
+  const unsigned long long m = e ? (frac | (1ull << 52)) : frac;
+  const int sh = 1075 - (e ? e : 1) - k;  // d 2^k = m 2^-sh
+  if (sh <= 0) return kQMax - 1;          // >= 2^52
+  if (sh >= 64) return 0;
+  const unsigned long long t = m >> sh;
+  return t >= kQMax ? kQMax - 1 : (uint32_t)t;
+}
+
 template <bool FOREST>
 __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos, int n,
                                                  const int32_t *__restrict__ offs, int S,
@@ -170,14 +195,13 @@ __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos,
   if (i >= n) return;
   int s = FOREST ? sys_of(offs, S, i) : 0;
   Frame f = frame[s];
-  double scale = __ddiv_rn((double)kQMax, f.w);  // exact: both are powers of two
+  // scale = 2^20 / L = 2^k exactly (L is a power of two, possibly subnormal)
+  const unsigned long long lb = (unsigned long long)__double_as_longlong(f.w);
+  const int le = (int)((lb >> 52) & 0x7ffull);
+  const int k = 20 - (le ? le - 1023 : -1074 + (63 - __clzll((long long)lb)));
   double o[3] = {f.x, f.y, f.z};
   uint32_t q[3];
-  for (int a = 0; a < 3; ++a) {
-    double t = floor(__dmul_rn(__dsub_rn(pos[3 * (size_t)i + a], o[a]), scale));
-    t = fmin(fmax(t, 0.0), (double)(kQMax - 1));
-    q[a] = (uint32_t)t;
-  }
+  for (int a = 0; a < 3; ++a) q[a] = quantize(__dsub_rn(pos[3 * (size_t)i + a], o[a]), k);
   key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
   idx[i] = (uint32_t)i;
 }
@@ -498,7 +522,6 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, const int32_t *__restric
                                                  uint32_t *c_ctr, int32_t *sys_root, int32_t *g_beg, int32_t *g_sys,
                                                  int32_t *counts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
   const int w = i >> 5;
   const bool ok = i < n;
   const unsigned lt = lanemask_lt();

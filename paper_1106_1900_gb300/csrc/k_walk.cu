@@ -618,6 +618,11 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     const int g = A.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
     const int4 L = A.g_list[g];
+    {  // pull the group's lists from DRAM into L2 now (one 128-byte line per 32 entries)
+      const uint32_t *lst = A.pool + (unsigned)L.x;
+      const int tot = L.y + L.z;
+      for (int i = 32 * lane; i < tot; i += 32 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(lst + i));
+    }
     const int gb0 = A.g_beg[g];
     const int ng = A.g_beg[g + 1] - gb0;
     float cx = 0.f, cy = 0.f, cz = 0.f;
