@@ -39,11 +39,17 @@ FLOPS_PP = 20
 FLOPS_PC = 54
 SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
-# algorithmic HBM bytes of the build phases of one step (frame + keys, sort,
-# move, cells + links + groups, moments, leapfrog predict + correct); counted
-# from what each kernel must read and write once
-BUILD_BYTES_PER_BODY = 724
-BUILD_BYTES_PER_CELL = 216
+# Algorithmic HBM bytes of the build phases and the leapfrog of one step:
+# what each kernel must read and write once.  Per body: predict 112 (x, v,
+# a_old read; x, v written), bbox 32 (x, m), keys 36 (x; key, index), sort
+# histogram 8 + eight passes of 24 (key and index, read and written), move 188
+# (80 gathered, 108 written: two-float positions, state, ids), levels + scan +
+# emit 14 (key, flags, per-warp counts), moments 32 (two-float positions),
+# correct 96 (v, a, a_old read; v, a written): 710.  Per cell: emit 20, link
+# 36, moments 128 (record written, children's records read): 184 (the opening
+# radii belong to the walk phase).  Per group: begin and system, 8.
+BUILD_BYTES_PER_BODY = 710
+BUILD_BYTES_PER_CELL = 184
 BUILD_BYTES_PER_GROUP = 8
 HBM_FALLBACK_GBS = 6800.0
 

@@ -54,7 +54,8 @@ typedef struct bh_params {
     int32_t n_leaf;         /* N_leaf: a cell with <= n_leaf bodies is a leaf (§2.1).
                                1..64, default 16. */
     int32_t n_crit;         /* N_crit: a group holds <= n_crit bodies (§2.2).
-                               n_leaf..64, default 64. */
+                               n_leaf..256, default 64 (groups of more than
+                               64 bodies are evaluated in several passes). */
     int32_t stack_capacity; /* entries per breadth-first level stack of one walking
                                warp (§2.2 current/next-level stacks), default 16384 */
     int32_t walk_variant;   /* 0: FP32 in group-relative coordinates with compensated

@@ -28,6 +28,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--ftz=true", "-Xcompiler", "-fPIC", "-I" + _INCLUDE]
 
 BH_OK = 0
+STATUS_CAPACITY = 2
 BH_NPHASES = 9
 PHASES = ("frame+keys", "sort", "move", "cells+link+groups", "moments", "walk", "leapfrog", "call",
           "walk eval")

@@ -2,9 +2,10 @@
 
 The paper fixes N_leaf = 16 (§2.1) and N_crit "typically 64" (§2.2) for its
 GPUs.  On a GB300 the best pair depends on the workload: smaller groups
-shorten every body's interaction lists and fill the walk's 64 slots per warp
-better, at the price of more walks.  For one workload (bodies on the device)
-and (theta, eps) this module:
+shorten every body's interaction lists, larger ones share one walk among
+more bodies (groups of more than 64 bodies are evaluated in several passes
+over their lists).  For one workload (bodies on the device) and (theta, eps)
+this module:
 
 * times the full leapfrog step (one CUDA graph replay per step) for each
   (n_leaf, n_crit) of a grid;
@@ -28,7 +29,7 @@ import sys
 
 TUNED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 PAPER_PAIR = (16, 64)
-DEFAULT_GRID = [(nl, nc) for nc in (8, 12, 16, 24, 32, 48, 64) for nl in (4, 8, 16) if nl <= nc]
+DEFAULT_GRID = [(nl, nc) for nc in (16, 32, 48, 64, 96, 128, 192, 256) for nl in (4, 8, 16) if nl <= nc]
 
 
 def key_for(n: int, theta: float, kind: str = "plummer") -> str:
@@ -59,32 +60,57 @@ def _errors(acc, ref):
     return {"p50": float(q[0]), "p99": float(q[1]), "rms": float(torch.sqrt((e * e).mean()))}
 
 
-def measure(pos, vel, mass, theta, eps, dt, n_leaf, n_crit, steps, targets, ref_acc, device=0):
+def measure(pos, vel, mass, theta, eps, dt, n_leaf, n_crit, steps, targets, ref_acc, device=0, pool_per_body=None):
     """Error against the reference and the mean step time of one (n_leaf, n_crit)."""
     import torch
 
     from . import TreeCode
 
     n = pos.shape[0]
-    tc = TreeCode(n, device=device, n_leaf=n_leaf, n_crit=n_crit)
-    tc.build(pos, mass)
-    acc, _ = tc.compute_forces(theta, eps)
-    tc.check()
-    err = _errors(acc[targets.long()], ref_acc)
-    tc.set_state(pos, vel, mass)
-    for _ in range(2):
-        tc.step(dt, theta, eps, graph=True)
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record()
-    for _ in range(steps):
-        tc.step(dt, theta, eps, graph=True)
-    t1.record()
-    torch.cuda.synchronize()
-    tc.check()
-    ms = t0.elapsed_time(t1) / steps
-    tc.close()
-    return {"n_leaf": n_leaf, "n_crit": n_crit, "ms_per_step": ms, **err}
+    extra = {} if pool_per_body is None else {"pool_per_body": pool_per_body}
+    tc = TreeCode(n, device=device, n_leaf=n_leaf, n_crit=n_crit, **extra)
+    try:
+        tc.build(pos, mass)
+        acc, _ = tc.compute_forces(theta, eps)
+        tc.check()
+        err = _errors(acc[targets.long()], ref_acc)
+        tc.set_state(pos, vel, mass)
+        for _ in range(2):
+            tc.step(dt, theta, eps, graph=True)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(steps):
+            tc.step(dt, theta, eps, graph=True)
+        t1.record()
+        torch.cuda.synchronize()
+        tc.check()
+        ms = t0.elapsed_time(t1) / steps
+    finally:
+        tc.close()
+    out = {"n_leaf": n_leaf, "n_crit": n_crit, "ms_per_step": ms, **err}
+    if pool_per_body is not None:
+        out["pool_per_body"] = pool_per_body
+    return out
+
+
+def measure_or_skip(*args, **kw):
+    """measure(), retried once with a four times larger list pool when the
+    interaction lists overflow it (small groups at small theta); None when the
+    pair does not fit at all."""
+    from . import STATUS_CAPACITY, BHError, default_params
+
+    try:
+        return measure(*args, **kw)
+    except BHError as e:
+        if e.code != STATUS_CAPACITY:
+            raise
+    try:
+        return measure(*args, **kw, pool_per_body=4 * default_params().pool_per_body)
+    except BHError as e:
+        if e.code != STATUS_CAPACITY:
+            raise
+        return None
 
 
 def autotune(pos, vel, mass, theta, eps, dt=1.0 / 64, grid=None, steps=5, subsample=4096, seed=40, slack=1.05,
@@ -105,8 +131,11 @@ def autotune(pos, vel, mass, theta, eps, dt=1.0 / 64, grid=None, steps=5, subsam
     ref_acc, _ = direct_forces(pos, mass, targets, eps)
     trials = []
     for nl, nc in grid:
-        r = measure(pos, vel, mass, theta, eps, dt, nl, nc, steps, targets, ref_acc, device)
-        trials.append(r)
+        r = measure_or_skip(pos, vel, mass, theta, eps, dt, nl, nc, steps, targets, ref_acc, device)
+        if r is None:
+            r = {"n_leaf": nl, "n_crit": nc, "skipped": "interaction lists exceed the capacities"}
+        else:
+            trials.append(r)
         if log:
             log(r)
     paper = next(r for r in trials if (r["n_leaf"], r["n_crit"]) == PAPER_PAIR)

@@ -32,7 +32,7 @@ int cu(cudaError_t e) { return e == cudaSuccess ? BH_OK : BH_ERR_CUDA; }
 int validate_params(const bh_params *p) {
   if (!p) return BH_ERR_INVALID_ARG;
   if (p->n_leaf < 1 || p->n_leaf > 64) return BH_ERR_INVALID_ARG;
-  if (p->n_crit < p->n_leaf || p->n_crit > 64) return BH_ERR_INVALID_ARG;
+  if (p->n_crit < p->n_leaf || p->n_crit > bh::kMaxCrit) return BH_ERR_INVALID_ARG;
   if (p->stack_capacity < 64) return BH_ERR_INVALID_ARG;
   if (p->walk_variant < 0 || p->walk_variant > 2) return BH_ERR_INVALID_ARG;
   if (p->walk_warps != 4) return BH_ERR_INVALID_ARG;  // the walk kernels are compiled for 4-warp blocks

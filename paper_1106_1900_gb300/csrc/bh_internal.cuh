@@ -14,6 +14,7 @@ constexpr int kRows = kLevels + 2;  // 21 cell levels + one row of group starts
 constexpr uint32_t kQMax = 1u << 20;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCostBuckets = 256;  // logarithmic buckets of a group's estimated evaluation cost
+constexpr int kMaxCrit = 256;      // largest group size N_crit (the level build's window halo)
 
 // Frame of one system: origin (per-axis minimum) and power-of-two side L.
 struct __align__(32) Frame {

@@ -94,18 +94,20 @@ __device__ __forceinline__ float two_diff(float a, float b, float &err) {
 __device__ __forceinline__ int pair_stride(int n) { return (n > 32) ? 32 : max((n + 1) >> 1, 1); }
 __device__ __forceinline__ int slots_per_body(int n) { return 32 / pair_stride(n); }
 
-// Passes over a group's lists.  A group of 33..63 bodies gets one slot per
-// body and leaves 64 - n slots idle; P passes over subsets of ceil(n / P)
-// bodies each, all on the group's own lists (a list valid for a group is valid
-// for any subset of it), fill the slots better.  A pass costs ceil(32 / k)
-// iterations per 32-entry tile, but no less than ~8: below that the tile's
-// gather from L2 is no longer hidden behind its arithmetic, and every pass
-// re-gathers the lists.  So smaller groups keep one pass, and 33..42 bodies
-// take two, 43..48 three.
+// Passes over a group's lists.  A warp holds at most 64 targets, so a group
+// of n > 64 bodies needs at least ceil(n / 64) passes; a group of 33..63
+// bodies gets one slot per body and leaves 64 - n slots idle.  P passes over
+// subsets of ceil(n / P) bodies each, all on the group's own lists (a list
+// valid for a group is valid for any subset of it), fill the slots better.  A
+// pass costs ceil(32 / k) iterations per 32-entry tile, but no less than ~8:
+// below that the tile's gather from L2 is no longer hidden behind its
+// arithmetic, and every pass re-gathers the lists.  So groups of up to 32
+// bodies keep one pass, 33..42 bodies take two, 43..48 three.
 __device__ __forceinline__ int eval_passes(int n) {
   if (n <= 32) return 1;
-  int best = 1, best_cost = 1 << 30;
-  for (int P = 1; P <= 4; ++P) {
+  const int p0 = (n + 63) / 64;
+  int best = p0, best_cost = 1 << 30;
+  for (int P = p0; P <= p0 + 3; ++P) {
     const int nb = (n + P - 1) / P;
     const int k = slots_per_body(nb);
     const int cost = P * (max((32 + k - 1) / k, 8) + 1);

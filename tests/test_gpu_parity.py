@@ -91,7 +91,8 @@ def test_eps_zero(cuda_lib):
     _full_parity(cuda_lib, pos, m, 0.5, 0.0)
 
 
-@pytest.mark.parametrize("n_leaf,n_crit", [(1, 1), (4, 8), (8, 32), (16, 16), (32, 64), (64, 64)])
+@pytest.mark.parametrize("n_leaf,n_crit", [(1, 1), (4, 8), (8, 32), (16, 16), (32, 64), (64, 64), (16, 96),
+                                           (16, 128), (8, 256)])
 def test_parameters(cuda_lib, n_leaf, n_crit):
     pos, _, m = ics.plummer(3000, 9)
     _full_parity(cuda_lib, pos, m, 0.6, 0.01, n_leaf=n_leaf, n_crit=n_crit)

@@ -209,7 +209,7 @@ def test_tree_matches_brute_force_plummer(n, seed):
     _check_tree(t, 16, 64)
 
 
-@pytest.mark.parametrize("n_leaf,n_crit", [(1, 1), (4, 8), (8, 32), (16, 16), (32, 64)])
+@pytest.mark.parametrize("n_leaf,n_crit", [(1, 1), (4, 8), (8, 32), (16, 16), (32, 64), (16, 128), (8, 256)])
 def test_tree_parameters(n_leaf, n_crit):
     pos, _, m = ics.plummer(700, 9)
     t = oracle.build_tree(pos, m, n_leaf=n_leaf, n_crit=n_crit)
