@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kBlock) k_move_state(const uint32_t *__restric
 }
 
 // ---------------------------------------------------------------- cells
-constexpr int kHalo = 64;  // >= N_crit >= N_leaf
+constexpr int kHalo = kMaxCrit;  // >= N_crit >= N_leaf
 
 // Per body: first level it starts a cell at (common prefix with the previous
 // key + 1), its leaf level, whether it starts a group; per warp: how many
