@@ -211,6 +211,7 @@ constexpr int kSortIpt = 16;
 constexpr int kSortTile = kBlock * kSortIpt;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kLookback = 8;  // predecessor tiles read per look-back step
 
 __device__ __forceinline__ uint32_t sort_digit(uint64_t k, uint32_t v, int pass, int key_passes,
                                                const int32_t *offs, int S) {
@@ -225,16 +226,9 @@ __global__ void __launch_bounds__(kBlock) k_sort_hist(const uint64_t *__restrict
   extern __shared__ uint32_t s_h[];  // [passes][256]
   for (int t = threadIdx.x; t < passes * 256; t += blockDim.x) s_h[t] = 0;
   __syncthreads();
-  const unsigned lane_lt = lanemask_lt();
-  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-    int i = base + threadIdx.x;
-    bool ok = i < n;
-    uint64_t k = ok ? key[i] : 0;
-    for (int p = 0; p < passes; ++p) {
-      uint32_t d = ok ? sort_digit(k, (uint32_t)i, p, key_passes, offs, S) : 256u;
-      unsigned peers = __match_any_sync(kFull, d);
-      if (ok && (peers & lane_lt) == 0) atomicAdd(&s_h[p * 256 + d], __popc(peers));
-    }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t k = key[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + sort_digit(k, (uint32_t)i, p, key_passes, offs, S)], 1u);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < passes * 256; t += blockDim.x)
@@ -346,21 +340,37 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(const uint64_t *__restrict
   s_tstart[t] = tstart;
   uint32_t excl = 0;
   if (tile > 0) {
+    // decoupled look-back, kLookback predecessors per step: their status
+    // words are loaded together, then summed from the nearest back to the
+    // first inclusive prefix; an unpublished one stops the step and is
+    // polled again (tile 0 is always inclusive, so the walk ends)
     int pr = (int)tile - 1;
     int spins = 0;
     while (pr >= 0) {
-      uint32_t w = __ldcv(&status[(size_t)pr * 256 + t]);
-      if ((w & ~kValMask) == 0) {
+      uint32_t w[kLookback];
+#pragma unroll
+      for (int q = 0; q < kLookback; ++q)
+        w[q] = (pr - q >= 0) ? __ldcv(&status[(size_t)(pr - q) * 256 + t]) : kFlagInc;
+      int q = 0;
+      bool found = false;
+      for (; q < kLookback; ++q) {
+        const uint32_t f = w[q] & ~kValMask;
+        if (f == 0) break;
+        excl += w[q] & kValMask;
+        if (f == kFlagInc) {
+          found = true;
+          break;
+        }
+      }
+      if (found) break;
+      if (q == 0) {
         if (++spins > kSpinLimit) {
           set_status(err, BH_ERR_TIMEOUT);
           break;
         }
         __nanosleep(32);
-        continue;
       }
-      excl += w & kValMask;
-      if ((w & ~kValMask) == kFlagInc) break;
-      --pr;
+      pr -= q;
     }
     atomicExch(&my[t], kFlagInc | (excl + tot));
   }
