@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="launch kernel by kernel instead of the graph")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--untuned", action="store_true", help="use the paper's N_leaf = 16, N_crit = 64")
+    ap.add_argument("--split", action="store_true",
+                    help="split walk (lists through a pool, then a separate evaluation kernel)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
     ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy"],
                     help="plummer: N-body Plummer sphere (--n); galaxy: Hernquist sphere + exponential disk, "
@@ -156,12 +158,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def walk_traffic():
-    """Per-launch DRAM bytes of the walk kernel from the committed ncu summary,
-    if it was taken from the current source of the kernel."""
+def walk_traffic(summary="walk_plummer_1m.md"):
+    """Per-launch DRAM bytes of the dominant walk kernel from the committed ncu
+    summary, if it was taken from the current source of the kernel."""
     src = open(os.path.join(ROOT, "paper_1106_1900_gb300", "csrc", "k_walk.cu"), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "eval_plummer_1m.md")
+    path = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -356,7 +358,8 @@ def main():
     from paper_1106_1900_gb300 import autotune
 
     tuned = None if args.untuned else autotune.tuned_params(n, args.theta, args.workload)
-    tc = bh.TreeCode(n, device=local, **(tuned or {}))
+    kw = dict(tuned or {}, walk_split=int(args.split))
+    tc = bh.TreeCode(n, device=local, **kw)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
     with torch.cuda.stream(stream):
@@ -409,7 +412,7 @@ def main():
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
     achieved = flops / eval_s if eval_s > 0 else 0.0  # the dominant kernel: k_eval
     achieved_walk = flops / walk_s if walk_s > 0 else 0.0
-    traffic = walk_traffic()
+    traffic = walk_traffic("eval_plummer_1m.md" if args.split else "walk_plummer_1m.md")
     clocks = clk.summary()
     mean_phase = {k: statistics.mean(p[k] for p in phases) for k in bh.PHASES if k != "call"}
     # build phases against HBM bandwidth
@@ -430,7 +433,7 @@ def main():
         hm = torch.from_numpy(m).pin_memory()
         ha = torch.empty((n, 3), dtype=torch.float32).pin_memory()
         hq = torch.empty(n, dtype=torch.float32).pin_memory()
-        tc2 = bh.TreeCode(n, device=local, **(tuned or {}))
+        tc2 = bh.TreeCode(n, device=local, **kw)
         for _ in range(max(1, args.warmup)):
             tc2.forces_host(hp, hm, args.theta, eps, ha, hq, stream=stream)
         if world > 1:
@@ -463,14 +466,17 @@ def main():
                    "cells": cnt["cells"], "groups": cnt["groups"], "graph": not args.eager},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
-                     "kernel": "k_eval (interaction lists -> accelerations, potentials)",
+                     "kernel": ("k_eval (interaction lists -> accelerations, potentials)" if args.split else
+                                "k_walk (per group: breadth-first walk into the warp's scratch, then the "
+                                "evaluation of its lists)"),
                      "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{SM_MAX_MHZ:.0f} MHz (unit counts and max clock)",
                      "flops_per_step": flops / args.steps, "pp_per_step": pp / args.steps,
                      "pc_per_step": pc / args.steps, "eval_ms_mean": statistics.mean(eval_ms),
                      "walk_phase": {"ms_mean": statistics.mean(walk_ms), "achieved": achieved_walk / 1e12,
                                     "frac": achieved_walk / peak if peak else None,
-                                    "what": "opening radii + k_traverse + k_eval"}},
+                                    "what": ("opening radii + k_traverse + k_order + k_eval" if args.split
+                                             else "opening radii + group order + k_walk")}},
         "phase_ms_mean": mean_phase,
         "build": build,
         "e2e": e2e,

@@ -67,7 +67,13 @@ typedef struct bh_params {
     int32_t list_capacity;  /* longest cell list and longest particle list of one
                                group (§2.2 interaction lists), default 16384 */
     int32_t pool_per_body;  /* interaction-list pool entries per body (the lists of
-                               all groups of one walk), default 768 */
+                               all groups of one walk, split walk only), default 768 */
+    int32_t walk_split;     /* 0: one fused kernel walks each group and evaluates its
+                               lists from the walking warp's scratch (default);
+                               1: a walk kernel writes every group's lists to the pool,
+                               an evaluation kernel reads them (most expensive group
+                               first).  Variant 2 always uses the split form.  Both
+                               give bit-identical results. */
 } bh_params;
 
 typedef struct bh_ctx bh_ctx; /* opaque, library-owned host object */

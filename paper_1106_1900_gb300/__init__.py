@@ -101,6 +101,7 @@ class bh_params(ctypes.Structure):
         ("walk_blocks_per_sm", ctypes.c_int32),
         ("list_capacity", ctypes.c_int32),
         ("pool_per_body", ctypes.c_int32),
+        ("walk_split", ctypes.c_int32),
     ]
 
 

@@ -38,6 +38,7 @@ int validate_params(const bh_params *p) {
   if (p->walk_warps != 4) return BH_ERR_INVALID_ARG;  // the walk kernels are compiled for 4-warp blocks
   if (p->walk_blocks_per_sm < 0 || p->walk_blocks_per_sm > 64) return BH_ERR_INVALID_ARG;
   if (p->list_capacity < 64 || p->pool_per_body < 1) return BH_ERR_INVALID_ARG;
+  if (p->walk_split != 0 && p->walk_split != 1) return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
 
@@ -67,22 +68,26 @@ int plan(Ctx &c, const bh_params *p, int64_t n_max, int32_t s_max, int device) {
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return BH_ERR_CUDA;
   c.num_sms = prop.multiProcessorCount;
   c.walk_smem = bh::walk_smem_bytes(bh::walk_block_warps());
-  int tb = p->walk_blocks_per_sm, eb = p->walk_blocks_per_sm;
+  int tb = p->walk_blocks_per_sm, eb = p->walk_blocks_per_sm, fb = p->walk_blocks_per_sm;
   {
-    int dev0 = 0, t_occ = 1, e_occ = 1;
+    int dev0 = 0, t_occ = 1, e_occ = 1, f_occ = 1;
     cudaGetDevice(&dev0);
     cudaSetDevice(device);
-    bh::walk_grids(&t_occ, &e_occ);
+    bh::walk_grids(&t_occ, &e_occ, &f_occ);
     cudaSetDevice(dev0);
     if (tb == 0) tb = t_occ;
     if (eb == 0) eb = e_occ;
+    if (fb == 0) fb = f_occ;
   }
-  // a small system needs fewer traversal warps (each owns stack and list scratch)
+  // a small system needs fewer walking warps (each owns stack and list scratch)
   const int64_t want = std::max<int64_t>(c.num_sms, (n_max + 63) / 64);
   c.trav_grid = (int)std::min<int64_t>((int64_t)c.num_sms * tb, want);
   c.eval_grid = (int)std::min<int64_t>((int64_t)c.num_sms * eb, want);
-  c.trav_warps_total = c.trav_grid * bh::walk_block_warps();
-  c.pool_cap = std::max<int64_t>((int64_t)p->pool_per_body * n_max, 1ll << 22);
+  c.walk_grid = (int)std::min<int64_t>((int64_t)c.num_sms * fb, want);
+  const bool fused = bh::walk_is_fused(*p);
+  c.trav_warps_total = (fused ? c.walk_grid : c.trav_grid) * bh::walk_block_warps();
+  // the list pool serves the split walk only
+  c.pool_cap = fused ? 32 : std::max<int64_t>((int64_t)p->pool_per_body * n_max, 1ll << 22);
   c.sort_max_passes = bh::sort_passes_for(s_max);
   c.sort_tiles_max = bh::sort_tiles_for(n_max);
   return BH_OK;
@@ -308,6 +313,7 @@ int bh_default_params(bh_params *p) {
   p->walk_blocks_per_sm = 0;
   p->list_capacity = 16384;
   p->pool_per_body = 768;
+  p->walk_split = 0;
   return BH_OK;
 }
 

@@ -29,9 +29,10 @@ struct Ctx {
   int64_t n_max = 0;
   int32_t s_max = 1;
   int64_t c_max = 0;   // cell-table bound
-  int trav_grid = 0;   // persistent traversal blocks
-  int eval_grid = 0;   // persistent evaluation blocks
-  int trav_warps_total = 0;
+  int trav_grid = 0;   // persistent traversal blocks (split walk)
+  int eval_grid = 0;   // persistent evaluation blocks (split walk)
+  int walk_grid = 0;   // persistent blocks of the fused walk
+  int trav_warps_total = 0;  // warps that own a level stack and list scratch
   int walk_smem = 0;
   int64_t pool_cap = 0;  // interaction-list pool entries
   size_t ws_bytes = 0;
@@ -139,7 +140,9 @@ cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s);
 enum OutMode { kOutCaller = 0, kOutSorted = 1 };
 cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s);
 int walk_smem_bytes(int warps);
-void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm);
+void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blocks_per_sm);
+// the fused walk unless the split form is asked for or the FP64 evaluation needs the pool
+inline bool walk_is_fused(const bh_params &p) { return p.walk_split == 0 && p.walk_variant != 2; }
 int walk_block_warps();
 cudaError_t walk_init_attrs(int smem);
 cudaError_t build_init_attrs();

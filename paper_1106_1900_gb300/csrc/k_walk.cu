@@ -91,8 +91,8 @@ __device__ __forceinline__ float two_diff(float a, float b, float &err) {
 // Slot layout of a (sub)group of n <= 64 bodies on a warp's 64 slots: lane l
 // holds bodies b = l mod h and b + h (h = pair_stride(n)) in phase l div h, so
 // both slots of a lane read the same source; a body gets 32 / h slots.
-__device__ __forceinline__ int pair_stride(int n) { return (n > 32) ? 32 : max((n + 1) >> 1, 1); }
-__device__ __forceinline__ int slots_per_body(int n) { return 32 / pair_stride(n); }
+__host__ __device__ constexpr int pair_stride(int n) { return (n > 32) ? 32 : ((n + 1) >> 1 > 1 ? (n + 1) >> 1 : 1); }
+__host__ __device__ constexpr int slots_per_body(int n) { return 32 / pair_stride(n); }
 
 // Passes over a group's lists.  A warp holds at most 64 targets, so a group
 // of n > 64 bodies needs at least ceil(n / 64) passes; a group of 33..63
@@ -102,15 +102,17 @@ __device__ __forceinline__ int slots_per_body(int n) { return 32 / pair_stride(n
 // pass costs ceil(32 / k) iterations per 32-entry tile, but no less than ~8:
 // below that the tile's gather from L2 is no longer hidden behind its
 // arithmetic, and every pass re-gathers the lists.  So groups of up to 32
-// bodies keep one pass, 33..42 bodies take two, 43..48 three.
-__device__ __forceinline__ int eval_passes(int n) {
+// bodies keep one pass, 33..42 bodies take two, 43..48 three.  The rule is
+// tabulated for n = 0..kMaxCrit at compile time (c_passes).
+__host__ __device__ constexpr int passes_rule(int n) {
   if (n <= 32) return 1;
   const int p0 = (n + 63) / 64;
   int best = p0, best_cost = 1 << 30;
   for (int P = p0; P <= p0 + 3; ++P) {
     const int nb = (n + P - 1) / P;
     const int k = slots_per_body(nb);
-    const int cost = P * (max((32 + k - 1) / k, 8) + 1);
+    const int it = (32 + k - 1) / k;
+    const int cost = P * ((it > 8 ? it : 8) + 1);
     if (cost < best_cost) {
       best_cost = cost;
       best = P;
@@ -119,6 +121,16 @@ __device__ __forceinline__ int eval_passes(int n) {
   const int nb = (n + best - 1) / best;
   return (n + nb - 1) / nb;  // no empty last pass
 }
+
+struct PassTable {
+  uint8_t p[kMaxCrit + 1];
+  constexpr PassTable() : p() {
+    for (int n = 0; n <= kMaxCrit; ++n) p[n] = (uint8_t)passes_rule(n);
+  }
+};
+__constant__ PassTable c_passes = PassTable();
+
+__device__ __forceinline__ int eval_passes(int n) { return c_passes.p[min(max(n, 0), kMaxCrit)]; }
 
 // Logarithmic bucket of an estimated cost w >= 1: eight buckets per octave,
 // increasing with w, below kCostBuckets for any int.
@@ -196,22 +208,19 @@ __device__ __forceinline__ void copy_list(uint32_t *__restrict__ dst, const int 
   }
 }
 
-template <int VAR>
-__global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
-  const int lane = threadIdx.x & 31;
-  const size_t gw = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  int *cur = A.stack + gw * 2 * (size_t)A.cap;
-  int *nxt = cur + A.cap;
-  int *cl = A.scratch + gw * 2 * (size_t)A.list_cap;
-  int *pl = cl + A.list_cap;
-  const unsigned lt = lanemask_lt();
-  const int G = A.counts[1];
+// One group's walk (§2.2) by one warp: cell list to cl, particle list to pl
+// (the warp's scratch, list_cap entries each), level stacks cur/nxt.  Returns
+// the full list lengths (which may exceed list_cap: then only the first
+// list_cap entries are stored) and the warp-reduced index sums.
+struct Walked {
+  int ncell, npart;
+  unsigned long long csum, psum;
+};
 
-  while (true) {
-    int g = 0;
-    if (lane == 0) g = (int)atomicAdd(A.queue, 1u);
-    g = __shfl_sync(kFull, g, 0);
-    if (g >= G) break;
+template <int VAR>
+__device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int lane, unsigned lt, int *cur, int *nxt,
+                                                 int *cl, int *pl) {
+  {
     const int gb = A.g_beg[g];
     const int n = A.g_beg[g + 1] - gb;
     // group centre and tight bounding box (offsets from the centre, rounded)
@@ -243,7 +252,6 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
     }
     int ncell = 0, npart = 0;
     unsigned long long csum = 0, psum = 0;
-    bool full = false;
     // ---- breadth-first walk from the root of the group's system (§2.2)
     if (lane == 0) cur[0] = A.sys_root[A.g_sys[g]];
     __syncwarp();
@@ -365,12 +373,54 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       nstk = t;
       ncur = nnext;
     }
-    if (ncell > A.list_cap || npart > A.list_cap) {
+    for (int o = 16; o > 0; o >>= 1) {
+      csum += __shfl_xor_sync(kFull, csum, o);
+      psum += __shfl_xor_sync(kFull, psum, o);
+    }
+    __syncwarp();
+    return Walked{ncell, npart, csum, psum};
+  }
+}
+
+// Per-group list statistics and the interaction counters (lane 0).
+__device__ __forceinline__ void record_group(const TravArgs &A, int g, int n, const Walked &w) {
+  A.g_npc[g] = w.ncell;
+  A.g_npp[g] = w.npart;
+  A.g_csum[g] = w.csum;
+  A.g_psum[g] = w.psum;
+  // every body of the group is on its own particle list once (its own
+  // leaves are always opened for theta < 1.15): that self pair is not counted
+  const unsigned long long self = (w.npart >= n) ? (unsigned long long)n : 0ull;
+  atomicAdd(&A.totals[0], (unsigned long long)n * (unsigned long long)w.npart - self);
+  atomicAdd(&A.totals[1], (unsigned long long)n * (unsigned long long)w.ncell);
+}
+
+// Split walk, first half: every group's lists into one pool at an exact
+// offset (one atomic per group), with an estimate of its evaluation cost.
+template <int VAR>
+__global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
+  const int lane = threadIdx.x & 31;
+  const size_t gw = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  int *cur = A.stack + gw * 2 * (size_t)A.cap;
+  int *nxt = cur + A.cap;
+  int *cl = A.scratch + gw * 2 * (size_t)A.list_cap;
+  int *pl = cl + A.list_cap;
+  const unsigned lt = lanemask_lt();
+  const int G = A.counts[1];
+
+  while (true) {
+    int g = 0;
+    if (lane == 0) g = (int)atomicAdd(A.queue, 1u);
+    g = __shfl_sync(kFull, g, 0);
+    if (g >= G) break;
+    const Walked w = traverse_group<VAR>(A, g, lane, lt, cur, nxt, cl, pl);
+    bool full = false;
+    if (w.ncell > A.list_cap || w.npart > A.list_cap) {
       full = true;
       if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
     }
     // ---- copy the lists into the pool at an exact offset
-    const int nc = min(ncell, A.list_cap), npp = min(npart, A.list_cap);
+    const int nc = min(w.ncell, A.list_cap), npp = min(w.npart, A.list_cap);
     unsigned long long off = 0;
     if (lane == 0) off = atomicAdd(A.pool_ctr, (unsigned long long)(nc + npp));
     off = __shfl_sync(kFull, off, 0);
@@ -383,29 +433,30 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       copy_list(A.pool + off, cl, nc, lane);
       copy_list(A.pool + off + nc, pl, npp, lane);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      csum += __shfl_xor_sync(kFull, csum, o);
-      psum += __shfl_xor_sync(kFull, psum, o);
-    }
     if (lane == 0) {
+      const int n = A.g_beg[g + 1] - A.g_beg[g];
       // evaluation cost ~ (2 cells + 1 body per list entry) / slots per body
       const int P = eval_passes(n);
       const int k = slots_per_body((n + P - 1) / P);
       const int work = full ? 1 : P * ((2 * nc + npp + k - 1) / k + 1);
       A.g_list[g] = full ? make_int4(0, 0, 0, work) : make_int4((int)off, nc, npp, work);
       atomicAdd(&A.work_hist[cost_bucket(work)], 1u);
-      A.g_npc[g] = ncell;
-      A.g_npp[g] = npart;
-      A.g_csum[g] = csum;
-      A.g_psum[g] = psum;
-      // every body of the group is on its own particle list once (its own
-      // leaves are always opened for theta < 1.15): that self pair is not counted
-      const unsigned long long self = (npart >= n) ? (unsigned long long)n : 0ull;
-      atomicAdd(&A.totals[0], (unsigned long long)n * (unsigned long long)npart - self);
-      atomicAdd(&A.totals[1], (unsigned long long)n * (unsigned long long)ncell);
+      record_group(A, g, n, w);
     }
     __syncwarp();
   }
+}
+
+// Bucket of a group of n bodies for the fused walk's order (its cost is not
+// known before its walk; the body count is the best early estimate).
+__device__ __forceinline__ int size_bucket(int n) { return min(max(n, 0), kCostBuckets - 1); }
+
+// Histogram of the group sizes (fused walk).
+__global__ void __launch_bounds__(256) k_size_hist(const int32_t *__restrict__ counts,
+                                                    const int32_t *__restrict__ g_beg, uint32_t *work_hist) {
+  const int G = counts[1];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+    atomicAdd(&work_hist[size_bucket(g_beg[g + 1] - g_beg[g])], 1u);
 }
 
 // Places the groups in order of decreasing estimated cost: the groups of
@@ -413,8 +464,10 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
 // within the bucket; a group's result does not depend on when it is taken).
 // Every block recomputes the bucket offsets from the histogram; appends are
 // aggregated per warp over lanes of equal bucket.
+template <bool BY_SIZE>
 __global__ void __launch_bounds__(kCostBuckets) k_order(const int32_t *__restrict__ counts,
-                                                         const int4 *__restrict__ g_list, uint32_t *work_hist,
+                                                         const int4 *__restrict__ g_list,
+                                                         const int32_t *__restrict__ g_beg, uint32_t *work_hist,
                                                          int32_t *order) {
   __shared__ uint32_t s_start[kCostBuckets];
   __shared__ uint32_t s_warp[kCostBuckets / 32];
@@ -437,7 +490,7 @@ __global__ void __launch_bounds__(kCostBuckets) k_order(const int32_t *__restric
   const unsigned lt = lanemask_lt();
   for (int base = blockIdx.x * blockDim.x; base < G; base += gridDim.x * blockDim.x) {
     const int g = base + t;
-    const int b = (g < G) ? cost_bucket(g_list[g].w) : -1;
+    const int b = (g >= G) ? -1 : BY_SIZE ? size_bucket(g_beg[g + 1] - g_beg[g]) : cost_bucket(g_list[g].w);
     const unsigned peers = __match_any_sync(kFull, b);
     const int leader = __ffs(peers) - 1;
     uint32_t first = 0;
@@ -592,15 +645,10 @@ __device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0,
   a.z = __ffma2_rn(qz, ri5, __ffma2_rn(coef, dz, a.z));
 }
 
-template <int VAR, bool GUARD, int MODE>
-__global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
-  extern __shared__ EvalSmem s_eval[];
-  const int lane = threadIdx.x & 31;
-  EvalSmem &S = s_eval[threadIdx.x >> 5];
-  const float2 e2 = f2(A.eps2, A.eps2);
-  const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);  // far away, zero mass, no quadrupole
+// Shared-memory staging: entries 32..kStage-1 are permanent nulls (zero mass, far away).
+__device__ __forceinline__ void init_stage(EvalSmem &S, int lane) {
+  const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  // entries 32..kStage-1 of the staging arrays are permanent nulls
   if (lane < kStage - 32) {
     S.sc[32 + lane][0] = null_src;
     S.sc[32 + lane][1] = zero4;
@@ -610,8 +658,223 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     S.pidx[32 + lane] = -1;
   }
   __syncwarp();
+}
+
+// Accelerations and potentials of group g's bodies from its cell list
+// clist[0..nc) and particle list plist[0..np), by one warp.
+template <int VAR, bool GUARD, int MODE>
+__device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int lane, int g,
+                                           const uint32_t *clist, int nc, const uint32_t *plist, int np) {
+  const float2 e2 = f2(A.eps2, A.eps2);
+  const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);  // far away, zero mass, no quadrupole
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int gb0 = A.g_beg[g];
+  const int ng = A.g_beg[g + 1] - gb0;
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  if (VAR == 0) {
+    const float4 c = A.part_hi[gb0];
+    cx = c.x;
+    cy = c.y;
+    cz = c.z;
+  }
+  const int npass = eval_passes(ng);
+  const int nbp = (ng + npass - 1) / npass;
+  for (int pass = 0; pass < npass; ++pass) {
+    // this pass: bodies gb .. gb + n - 1 of the group, on the group's lists
+    const int gb = gb0 + pass * nbp;
+    const int n = min(nbp, ng - pass * nbp);
+    // lane -> (phase ph, bodies b0 and b1 = b0 + h): both slots read the same entry
+    const int h = pair_stride(n);
+    const int k = 32 / h;  // phases = slots per body
+    const int ph = min(lane / h, k - 1);
+    const int b0 = lane % h, b1 = b0 + h;
+    const bool v0 = lane < h * k && b0 < n, v1 = lane < h * k && b1 < n;
+    Targets2 T;
+    {
+      const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
+      const Target t0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
+      const Target t1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
+      T.nhx = f2(-t0.hx, -t1.hx);
+      T.nhy = f2(-t0.hy, -t1.hy);
+      T.nhz = f2(-t0.hz, -t1.hz);
+      T.nlx = f2(-t0.lx, -t1.lx);
+      T.nly = f2(-t0.ly, -t1.ly);
+      T.nlz = f2(-t0.lz, -t1.lz);
+    }
+    S.ah[lane] = zero4;
+    S.al[lane] = zero4;
+    S.ah[32 + lane] = zero4;
+    S.al[32 + lane] = zero4;
+    Acc2 t;  // partial sums since the last fold
+    t.x = t.y = t.z = t.np = f2(0.f, 0.f);
+    int since = 0;  // interactions per slot since the last fold
+
+    // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
+    {
+      // indices run one tile ahead of the gathers, which run one tile ahead of
+      // the arithmetic: no gather waits on the load of its own address
+      float4 ra = zero4, rb = zero4, rq0 = zero4, rq1 = zero4;
+      if (lane < nc) {
+        const size_t ci = clist[lane];
+        ra = A.mom[4 * ci];
+        rb = A.mom[4 * ci + 1];
+        rq0 = A.mom[4 * ci + 2];
+        rq1 = A.mom[4 * ci + 3];
+      }
+      uint32_t ci_next = (32 + lane < nc) ? clist[32 + lane] : 0u;
+      for (int base = 0; base < nc; base += 32) {
+        const int cnt = min(32, nc - base);
+        if (lane < cnt) {
+          float dx, dy, dz;
+          if (VAR == 0) {
+            dx = (ra.x - cx) + rb.x;
+            dy = (ra.y - cy) + rb.y;
+            dz = (ra.z - cz) + rb.z;
+          } else {
+            dx = ra.x;
+            dy = ra.y;
+            dz = ra.z;
+          }
+          S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
+          S.sc[lane][1] = make_float4(-rq0.x, -rq0.y, -rq0.z, -rq0.w);
+          S.sc[lane][2] = make_float4(-rq1.x, -rq1.y, 0.f, 0.f);
+        } else {
+          S.sc[lane][0] = null_src;
+          S.sc[lane][1] = zero4;
+          S.sc[lane][2] = zero4;
+        }
+        if (base + 32 + lane < nc) {  // gather the next tile now
+          const size_t ci = ci_next;
+          ra = A.mom[4 * ci];
+          rb = A.mom[4 * ci + 1];
+          rq0 = A.mom[4 * ci + 2];
+          rq1 = A.mom[4 * ci + 3];
+        }
+        if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
+        __syncwarp();
+#pragma unroll 1
+        for (int j = ph; j < cnt + ph; j += k) {
+          const float4 *e = S.sc[j];
+          pc2(t, T, e[0], e[1], e[2], e2);
+        }
+        since += (cnt + k - 1) / k;
+        if (since >= 32) {
+          fold2<VAR>(S, lane, t);
+          since = 0;
+        }
+        __syncwarp();
+      }
+    }
+    // ---- particle list
+    {
+      float4 rh = zero4, rl = zero4;
+      int rb = -1;
+      if (lane < np) {
+        rb = (int)plist[lane];
+        rh = A.part_hi[rb];
+        rl = A.part_lo[rb];
+      }
+      int pb_next = (32 + lane < np) ? (int)plist[32 + lane] : -1;
+      for (int base = 0; base < np; base += 32) {
+        const int cnt = min(32, np - base);
+        bool member = false;
+        if (lane < cnt) {
+          member = (unsigned)(rb - gb) < (unsigned)n;
+          const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
+          S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
+          S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
+          S.pidx[lane] = rb;
+        } else {
+          S.sp[lane][0] = null_src;
+          S.sp[lane][1] = zero4;
+          S.pidx[lane] = -1;
+        }
+        if (base + 32 + lane < np) {  // gather the next tile now
+          rb = pb_next;
+          rh = A.part_hi[rb];
+          rl = A.part_lo[rb];
+        }
+        if (base + 64 + lane < np) pb_next = (int)plist[base + 64 + lane];
+        const bool self_tile = __any_sync(kFull, member);
+        __syncwarp();
+        if (self_tile) {
+          // a tile with the group's own bodies: skip each body's pair with itself by index
+          const int me0 = gb + b0, me1 = gb + b1;
+          for (int j = ph; j < cnt + ph; j += k) {
+            const float4 *e = S.sp[j];
+            pp2<VAR, GUARD, true>(t, T, e[0], e[1], e2, me0, me1, S.pidx[j]);
+          }
+        } else {
+#pragma unroll 2
+          for (int j = ph; j < cnt + ph; j += k) {
+            const float4 *e = S.sp[j];
+            pp2<VAR, GUARD, false>(t, T, e[0], e[1], e2);
+          }
+        }
+        since += (cnt + k - 1) / k;
+        if (since >= 32) {
+          fold2<VAR>(S, lane, t);
+          since = 0;
+        }
+        __syncwarp();
+      }
+    }
+    fold2<VAR>(S, lane, t);
+    __syncwarp();
+
+    // ---- combine the slots of each body and write
+    auto write_body = [&](int b, float ox, float oy, float oz, float op) {
+      const int gi = gb + b;
+      if (MODE == kOutSorted) {
+        A.acc_sorted[gi] = make_float4(ox, oy, oz, op);
+      } else {
+        const size_t j = A.perm[gi];
+        A.acc_out[3 * j] = ox;
+        A.acc_out[3 * j + 1] = oy;
+        A.acc_out[3 * j + 2] = oz;
+        A.pot_out[j] = op;
+      }
+    };
+    if (k == 1) {
+      if (v0) {
+        const float4 H = S.ah[lane], Lo = S.al[lane];
+        write_body(b0, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+      }
+      if (v1) {
+        const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
+        write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+      }
+    } else if (lane < n) {
+      // body b's slots: b + q h (q < k) in the first half of the slot array
+      // for b < h, b - h + q h in the second half otherwise
+      const int s0 = (lane < h) ? lane : 32 + lane - h;
+      float4 H = S.ah[s0], Lo = S.al[s0];
+      for (int q = 1; q < k; ++q) {
+        const float4 hq = S.ah[s0 + q * h], lq = S.al[s0 + q * h];
+        two_sum_into(H.x, Lo.x, hq.x);
+        two_sum_into(H.y, Lo.y, hq.y);
+        two_sum_into(H.z, Lo.z, hq.z);
+        two_sum_into(H.w, Lo.w, hq.w);
+        Lo.x += lq.x;
+        Lo.y += lq.y;
+        Lo.z += lq.z;
+        Lo.w += lq.w;
+      }
+      write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+    }
+    __syncwarp();
+  }  // passes
+}
+
+// Split walk, second half: every group's lists from the pool, most expensive
+// group first, so that the launch ends on cheap ones.
+template <int VAR, bool GUARD, int MODE>
+__global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
+  extern __shared__ EvalSmem s_eval[];
+  const int lane = threadIdx.x & 31;
+  EvalSmem &S = s_eval[threadIdx.x >> 5];
+  init_stage(S, lane);
   const int G = A.counts[1];
-  // groups are taken most expensive first, so that the launch ends on cheap ones
   while (true) {
     int q = 0;
     if (lane == 0) q = (int)atomicAdd(A.queue, 1u);
@@ -620,211 +883,47 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     const int g = A.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
     const int4 L = A.g_list[g];
-    {  // pull the group's lists from DRAM into L2 now (one 128-byte line per 32 entries)
-      const uint32_t *lst = A.pool + (unsigned)L.x;
-      const int tot = L.y + L.z;
-      for (int i = 32 * lane; i < tot; i += 32 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(lst + i));
-    }
-    const int gb0 = A.g_beg[g];
-    const int ng = A.g_beg[g + 1] - gb0;
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    if (VAR == 0) {
-      const float4 c = A.part_hi[gb0];
-      cx = c.x;
-      cy = c.y;
-      cz = c.z;
-    }
-    const int npass = eval_passes(ng);
-    const int nbp = (ng + npass - 1) / npass;
-    for (int pass = 0; pass < npass; ++pass) {
-      // this pass: bodies gb .. gb + n - 1 of the group, on the group's lists
-      const int gb = gb0 + pass * nbp;
-      const int n = min(nbp, ng - pass * nbp);
-      const uint32_t *clist = A.pool + (unsigned)L.x;
-      const uint32_t *plist = clist + L.y;
-      // lane -> (phase ph, bodies b0 and b1 = b0 + h): both slots read the same entry
-      const int h = pair_stride(n);
-      const int k = 32 / h;  // phases = slots per body
-      const int ph = min(lane / h, k - 1);
-      const int b0 = lane % h, b1 = b0 + h;
-      const bool v0 = lane < h * k && b0 < n, v1 = lane < h * k && b1 < n;
-      Targets2 T;
-      {
-        const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
-        const Target t0 = make_target<VAR>(A.part_hi[lb0], A.part_lo[lb0], cx, cy, cz);
-        const Target t1 = make_target<VAR>(A.part_hi[lb1], A.part_lo[lb1], cx, cy, cz);
-        T.nhx = f2(-t0.hx, -t1.hx);
-        T.nhy = f2(-t0.hy, -t1.hy);
-        T.nhz = f2(-t0.hz, -t1.hz);
-        T.nlx = f2(-t0.lx, -t1.lx);
-        T.nly = f2(-t0.ly, -t1.ly);
-        T.nlz = f2(-t0.lz, -t1.lz);
-      }
-      S.ah[lane] = zero4;
-      S.al[lane] = zero4;
-      S.ah[32 + lane] = zero4;
-      S.al[32 + lane] = zero4;
-      Acc2 t;  // partial sums since the last fold
-      t.x = t.y = t.z = t.np = f2(0.f, 0.f);
-      int since = 0;  // interactions per slot since the last fold
+    const uint32_t *lst = A.pool + (unsigned)L.x;
+    // pull the group's lists from DRAM into L2 now (one 128-byte line per 32 entries)
+    for (int i = 32 * lane; i < L.y + L.z; i += 32 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(lst + i));
+    eval_group<VAR, GUARD, MODE>(A, S, lane, g, lst, L.y, lst + L.y, L.z);
+  }
+}
 
-      // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
-      {
-        const int nc = L.y;
-        // indices run one tile ahead of the gathers, which run one tile ahead of
-        // the arithmetic: no gather waits on the load of its own address
-        float4 ra = zero4, rb = zero4, rq0 = zero4, rq1 = zero4;
-        if (lane < nc) {
-          const size_t ci = clist[lane];
-          ra = A.mom[4 * ci];
-          rb = A.mom[4 * ci + 1];
-          rq0 = A.mom[4 * ci + 2];
-          rq1 = A.mom[4 * ci + 3];
-        }
-        uint32_t ci_next = (32 + lane < nc) ? clist[32 + lane] : 0u;
-        for (int base = 0; base < nc; base += 32) {
-          const int cnt = min(32, nc - base);
-          if (lane < cnt) {
-            float dx, dy, dz;
-            if (VAR == 0) {
-              dx = (ra.x - cx) + rb.x;
-              dy = (ra.y - cy) + rb.y;
-              dz = (ra.z - cz) + rb.z;
-            } else {
-              dx = ra.x;
-              dy = ra.y;
-              dz = ra.z;
-            }
-            S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
-            S.sc[lane][1] = make_float4(-rq0.x, -rq0.y, -rq0.z, -rq0.w);
-            S.sc[lane][2] = make_float4(-rq1.x, -rq1.y, 0.f, 0.f);
-          } else {
-            S.sc[lane][0] = null_src;
-            S.sc[lane][1] = zero4;
-            S.sc[lane][2] = zero4;
-          }
-          if (base + 32 + lane < nc) {  // gather the next tile now
-            const size_t ci = ci_next;
-            ra = A.mom[4 * ci];
-            rb = A.mom[4 * ci + 1];
-            rq0 = A.mom[4 * ci + 2];
-            rq1 = A.mom[4 * ci + 3];
-          }
-          if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
-          __syncwarp();
-#pragma unroll 1
-          for (int j = ph; j < cnt + ph; j += k) {
-            const float4 *e = S.sc[j];
-            pc2(t, T, e[0], e[1], e[2], e2);
-          }
-          since += (cnt + k - 1) / k;
-          if (since >= 32) {
-            fold2<VAR>(S, lane, t);
-            since = 0;
-          }
-          __syncwarp();
-        }
-      }
-      // ---- particle list
-      {
-        const int np = L.z;
-        float4 rh = zero4, rl = zero4;
-        int rb = -1;
-        if (lane < np) {
-          rb = (int)plist[lane];
-          rh = A.part_hi[rb];
-          rl = A.part_lo[rb];
-        }
-        int pb_next = (32 + lane < np) ? (int)plist[32 + lane] : -1;
-        for (int base = 0; base < np; base += 32) {
-          const int cnt = min(32, np - base);
-          bool member = false;
-          if (lane < cnt) {
-            member = (unsigned)(rb - gb) < (unsigned)n;
-            const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
-            S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
-            S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
-            S.pidx[lane] = rb;
-          } else {
-            S.sp[lane][0] = null_src;
-            S.sp[lane][1] = zero4;
-            S.pidx[lane] = -1;
-          }
-          if (base + 32 + lane < np) {  // gather the next tile now
-            rb = pb_next;
-            rh = A.part_hi[rb];
-            rl = A.part_lo[rb];
-          }
-          if (base + 64 + lane < np) pb_next = (int)plist[base + 64 + lane];
-          const bool self_tile = __any_sync(kFull, member);
-          __syncwarp();
-          if (self_tile) {
-            // a tile with the group's own bodies: skip each body's pair with itself by index
-            const int me0 = gb + b0, me1 = gb + b1;
-            for (int j = ph; j < cnt + ph; j += k) {
-              const float4 *e = S.sp[j];
-              pp2<VAR, GUARD, true>(t, T, e[0], e[1], e2, me0, me1, S.pidx[j]);
-            }
-          } else {
-#pragma unroll 2
-            for (int j = ph; j < cnt + ph; j += k) {
-              const float4 *e = S.sp[j];
-              pp2<VAR, GUARD, false>(t, T, e[0], e[1], e2);
-            }
-          }
-          since += (cnt + k - 1) / k;
-          if (since >= 32) {
-            fold2<VAR>(S, lane, t);
-            since = 0;
-          }
-          __syncwarp();
-        }
-      }
-      fold2<VAR>(S, lane, t);
-      __syncwarp();
-
-      // ---- combine the slots of each body and write
-      auto write_body = [&](int b, float ox, float oy, float oz, float op) {
-        const int gi = gb + b;
-        if (MODE == kOutSorted) {
-          A.acc_sorted[gi] = make_float4(ox, oy, oz, op);
-        } else {
-          const size_t j = A.perm[gi];
-          A.acc_out[3 * j] = ox;
-          A.acc_out[3 * j + 1] = oy;
-          A.acc_out[3 * j + 2] = oz;
-          A.pot_out[j] = op;
-        }
-      };
-      if (k == 1) {
-        if (v0) {
-          const float4 H = S.ah[lane], Lo = S.al[lane];
-          write_body(b0, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
-        }
-        if (v1) {
-          const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
-          write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
-        }
-      } else if (lane < n) {
-        // body b's slots: b + q h (q < k) in the first half of the slot array
-        // for b < h, b - h + q h in the second half otherwise
-        const int s0 = (lane < h) ? lane : 32 + lane - h;
-        float4 H = S.ah[s0], Lo = S.al[s0];
-        for (int q = 1; q < k; ++q) {
-          const float4 hq = S.ah[s0 + q * h], lq = S.al[s0 + q * h];
-          two_sum_into(H.x, Lo.x, hq.x);
-          two_sum_into(H.y, Lo.y, hq.y);
-          two_sum_into(H.z, Lo.z, hq.z);
-          two_sum_into(H.w, Lo.w, hq.w);
-          Lo.x += lq.x;
-          Lo.y += lq.y;
-          Lo.z += lq.z;
-          Lo.w += lq.w;
-        }
-        write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
-      }
-      __syncwarp();
-    }  // passes
+// Fused walk: a warp walks a group into its own list scratch and evaluates
+// it from there at once, the next group's walk overlapping other warps'
+// evaluations on the same SM (the walk is issue- and latency-bound on the
+// integer and load pipes, the evaluation bound by the FP32 pipe).  No list
+// pool, no copy; groups are taken largest first.
+template <int VAR, bool GUARD, int MODE>
+__global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_walk(TravArgs T, EvalArgs E) {
+  extern __shared__ EvalSmem s_eval[];
+  const int lane = threadIdx.x & 31;
+  EvalSmem &S = s_eval[threadIdx.x >> 5];
+  init_stage(S, lane);
+  const size_t gw = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  int *cur = T.stack + gw * 2 * (size_t)T.cap;
+  int *nxt = cur + T.cap;
+  int *cl = T.scratch + gw * 2 * (size_t)T.list_cap;
+  int *pl = cl + T.list_cap;
+  const unsigned lt = lanemask_lt();
+  const int G = T.counts[1];
+  while (true) {
+    int q = 0;
+    if (lane == 0) q = (int)atomicAdd(E.queue, 1u);
+    q = __shfl_sync(kFull, q, 0);
+    if (q >= G) break;
+    const int g = E.order[q];
+    if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
+    const Walked w = traverse_group<VAR>(T, g, lane, lt, cur, nxt, cl, pl);
+    const bool full = w.ncell > T.list_cap || w.npart > T.list_cap;
+    if (lane == 0) {
+      if (full) set_status(T.status, BH_ERR_CAPACITY);
+      record_group(T, g, T.g_beg[g + 1] - T.g_beg[g], w);
+    }
+    __syncwarp();  // the lists written by every lane are visible to every lane
+    eval_group<VAR, GUARD, MODE>(E, S, lane, g, reinterpret_cast<const uint32_t *>(cl), full ? 0 : w.ncell,
+                                 reinterpret_cast<const uint32_t *>(pl), full ? 0 : w.npart);
   }
 }
 
@@ -906,14 +1005,21 @@ cudaError_t launch_eval(Ctx &c, const EvalArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int VAR, bool GUARD, int MODE>
+cudaError_t launch_fused(Ctx &c, const TravArgs &t, const EvalArgs &a, cudaStream_t s) {
+  k_walk<VAR, GUARD, MODE><<<c.walk_grid, kThreads, kWarps * sizeof(EvalSmem), s>>>(t, a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int walk_smem_bytes(int warps) { return warps * (int)sizeof(EvalSmem); }
 
 cudaError_t walk_init_attrs(int smem) {
   cudaError_t e = cudaSuccess;
-#define BH_EVAL_ATTR(V, G, M) \
-  if (!e) e = cudaFuncSetAttribute(k_eval<V, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+#define BH_EVAL_ATTR(V, G, M)                                                                        \
+  if (!e) e = cudaFuncSetAttribute(k_eval<V, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+  if (!e) e = cudaFuncSetAttribute(k_walk<V, G, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   BH_EVAL_ATTR(0, false, kOutCaller)
   BH_EVAL_ATTR(0, true, kOutCaller)
   BH_EVAL_ATTR(0, false, kOutSorted)
@@ -926,16 +1032,21 @@ cudaError_t walk_init_attrs(int smem) {
   return e;
 }
 
-void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm) {
-  int nt = 0, ne = 0;
+void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blocks_per_sm) {
+  int nt = 0, ne = 0, nf = 0;
   const int smem = kWarps * (int)sizeof(EvalSmem);
   cudaFuncSetAttribute(k_eval<0, false, kOutCaller>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_walk<0, false, kOutCaller>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, k_traverse<0>, kThreads, 0) != cudaSuccess) nt = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ne, k_eval<0, false, kOutCaller>, kThreads, smem) !=
       cudaSuccess)
     ne = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nf, k_walk<0, false, kOutCaller>, kThreads, smem) !=
+      cudaSuccess)
+    nf = 1;
   *trav_blocks_per_sm = nt > 0 ? nt : 1;
   *eval_blocks_per_sm = ne > 0 ? ne : 1;
+  *fused_blocks_per_sm = nf > 0 ? nf : 1;
 }
 
 int walk_block_warps() { return kWarps; }
@@ -967,20 +1078,6 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   t.g_psum = c.g_psum;
   t.totals = c.d_totals;
   t.status = c.d_status;
-  const int var = c.p.walk_variant;
-  if (var == 1) k_traverse<1><<<c.trav_grid, kThreads, 0, s>>>(t);
-  else k_traverse<0><<<c.trav_grid, kThreads, 0, s>>>(t);
-  cudaError_t e = cudaGetLastError();
-  c.launches++;
-  if (e) return e;
-  k_order<<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.work_hist, c.g_order);
-  e = cudaGetLastError();
-  c.launches++;
-  if (e) return e;
-  if (c.profiling) {
-    if (c.capturing) cudaEventRecordWithFlags(c.ev[8][0], s, cudaEventRecordExternal);
-    else cudaEventRecord(c.ev[8][0], s);
-  }
   EvalArgs a;
   a.part_hi = c.part_hi;
   a.part_lo = c.part_lo;
@@ -996,7 +1093,53 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   a.acc_out = acc;
   a.pot_out = pot;
   a.perm = c.idx[0];
+  const int var = c.p.walk_variant;
   const bool guard = !(a.eps2 > 0.f);
+  const bool fused = walk_is_fused(c.p);
+  cudaError_t e = cudaSuccess;
+  auto mark = [&](int end) {
+    if (!c.profiling) return;
+    if (c.capturing) cudaEventRecordWithFlags(c.ev[8][end], s, cudaEventRecordExternal);
+    else cudaEventRecord(c.ev[8][end], s);
+    if (end) c.phase_rec[8] = true;
+  };
+  if (fused) {
+    // groups by size (largest first), then one kernel walks and evaluates
+    k_size_hist<<<c.num_sms * 4, 256, 0, s>>>(c.d_counts, c.g_beg, c.work_hist);
+    e = cudaGetLastError();
+    c.launches++;
+    if (e) return e;
+    k_order<true><<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.g_beg, c.work_hist, c.g_order);
+    e = cudaGetLastError();
+    c.launches++;
+    if (e) return e;
+    mark(0);
+#define BH_WALK_CASE(V, G, M) \
+  if (var == V && guard == G && mode == M) e = launch_fused<V, G, M>(c, t, a, s); else
+    BH_WALK_CASE(0, false, kOutCaller)
+    BH_WALK_CASE(0, true, kOutCaller)
+    BH_WALK_CASE(0, false, kOutSorted)
+    BH_WALK_CASE(0, true, kOutSorted)
+    BH_WALK_CASE(1, false, kOutCaller)
+    BH_WALK_CASE(1, true, kOutCaller)
+    BH_WALK_CASE(1, false, kOutSorted)
+    BH_WALK_CASE(1, true, kOutSorted)
+    e = cudaErrorInvalidValue;
+#undef BH_WALK_CASE
+    mark(1);
+    c.launches++;
+    return e;
+  }
+  if (var == 1) k_traverse<1><<<c.trav_grid, kThreads, 0, s>>>(t);
+  else k_traverse<0><<<c.trav_grid, kThreads, 0, s>>>(t);
+  e = cudaGetLastError();
+  c.launches++;
+  if (e) return e;
+  k_order<false><<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.g_beg, c.work_hist, c.g_order);
+  e = cudaGetLastError();
+  c.launches++;
+  if (e) return e;
+  mark(0);
   if (var == 2) {
     if (mode == kOutSorted) k_eval_f64<kOutSorted><<<c.eval_grid, kThreads, 0, s>>>(a);
     else k_eval_f64<kOutCaller><<<c.eval_grid, kThreads, 0, s>>>(a);
@@ -1014,11 +1157,7 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   BH_EVAL_CASE(1, true, kOutSorted)
   e = cudaErrorInvalidValue;
 #undef BH_EVAL_CASE
-  if (c.profiling) {
-    if (c.capturing) cudaEventRecordWithFlags(c.ev[8][1], s, cudaEventRecordExternal);
-    else cudaEventRecord(c.ev[8][1], s);
-    c.phase_rec[8] = true;
-  }
+  mark(1);
   c.launches++;
   return e;
 }

@@ -259,6 +259,29 @@ def test_checkpoint_resume_is_bit_identical(cuda_lib):
     assert np.array_equal(x6, xr) and np.array_equal(v6, vr) and np.array_equal(a6, ar)
 
 
+@pytest.mark.parametrize("variant,n_crit", [(0, 64), (0, 96), (1, 64)])
+def test_fused_walk_equals_split_walk(cuda_lib, variant, n_crit):
+    """The fused walk (walk and evaluation in one kernel, lists in the warp's
+    scratch) and the split walk (lists through the pool) build the same lists
+    in the same order and evaluate them with the same code: identical bits."""
+    import torch
+
+    pos, _, m = ics.plummer(16384, 1)
+    P, M = torch.from_numpy(pos).cuda(), torch.from_numpy(m).cuda()
+    out = []
+    for split in (0, 1):
+        tc = cuda_lib.TreeCode(len(pos), walk_split=split, walk_variant=variant, n_crit=n_crit)
+        tc.build(P, M)
+        acc, pot = tc.compute_forces(0.5, 0.01)
+        tc.check()
+        out.append((acc.cpu().numpy(), pot.cpu().numpy(), tc.group_stats(), tc.counts()))
+    (a0, p0, g0, c0), (a1, p1, g1, c1) = out
+    assert np.array_equal(a0, a1) and np.array_equal(p0, p1)
+    for k in ("nc", "np", "csum", "psum"):
+        assert np.array_equal(g0[k], g1[k])
+    assert (c0["pp"], c0["pc"]) == (c1["pp"], c1["pc"])
+
+
 def test_forest_step_equals_systems(cuda_lib):
     pos, vel, m, off = ics.ensemble(n_sys=6, seed=7, n_min=500, n_max=4000)
     _, xf, vf, _, _ = _state_run(cuda_lib, pos, vel, m, 3, 1 / 64, 0.5, 0.01, offsets=off)
