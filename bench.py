@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--eager", action="store_true", help="launch kernel by kernel instead of the graph")
     ap.add_argument("--flush-mb", type=int, default=512, help="L2 flush buffer written between timed steps")
     ap.add_argument("--untuned", action="store_true", help="use the paper's N_leaf = 16, N_crit = 64")
+    ap.add_argument("--mac", type=int, default=0, choices=[0, 1],
+                    help="opening criterion: 0 Eq. 1 (default), 1 minimal distance")
     ap.add_argument("--split", action="store_true",
                     help="split walk (lists through a pool, then a separate evaluation kernel)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
@@ -358,7 +360,7 @@ def main():
     from paper_1106_1900_gb300 import autotune
 
     tuned = None if args.untuned else autotune.tuned_params(n, args.theta, args.workload)
-    kw = dict(tuned or {}, walk_split=int(args.split))
+    kw = dict(tuned or {}, walk_split=int(args.split), mac=args.mac)
     tc = bh.TreeCode(n, device=local, **kw)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
@@ -463,7 +465,9 @@ def main():
                    "l2": f"flushed between timed steps ({args.flush_mb} MB write)" if args.flush_mb else "not flushed",
                    "n_leaf": tc.params.n_leaf, "n_crit": tc.params.n_crit,
                    "params": "autotuned (paper_1106_1900_gb300/tuned.json)" if tuned else "paper defaults",
-                   "cells": cnt["cells"], "groups": cnt["groups"], "graph": not args.eager},
+                   "cells": cnt["cells"], "groups": cnt["groups"], "graph": not args.eager,
+                   "opening": "Eq. 1" if args.mac == 0 else "minimal distance",
+                   "walk": "split" if args.split else "fused"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,
                      "kernel": ("k_eval (interaction lists -> accelerations, potentials)" if args.split else

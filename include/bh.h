@@ -74,6 +74,11 @@ typedef struct bh_params {
                                an evaluation kernel reads them (most expensive group
                                first).  Variant 2 always uses the split form.  Both
                                give bit-identical results. */
+    int32_t mac;            /* opening criterion: 0: Eq. 1, d > l/theta + delta with d
+                               from the cell's centre of mass to the group's box
+                               (default); 1: the minimal-distance criterion (§2.3),
+                               d > l/theta with d between the cell's cube and the
+                               group's box (more interactions, smaller errors) */
 } bh_params;
 
 typedef struct bh_ctx bh_ctx; /* opaque, library-owned host object */

@@ -62,11 +62,12 @@ def _load():
                 "or_link": (ctypes.c_int, [i64, p, p, p, p, p, p, p]),
                 "or_groups": (i64, [i64, p, p, p, p, p, p, i32, i64, p, p]),
                 "or_moments": (ctypes.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p, p, p]),
-                "or_walk": (ctypes.c_int, [i64, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, p, p, i64, p, p,
-                                           dbl, dbl, p, p, p, p]),
+                "or_walk": (ctypes.c_int, [i64, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, p, p, p, i64, p,
+                                           p, dbl, dbl, i32, p, p, p, p]),
                 "or_direct": (ctypes.c_int, [i64, p, p, i32, p, i64, p, dbl, p, p]),
                 "or_cell_exact": (ctypes.c_int, [i64, i64, p, p, p, dbl, p, p]),
                 "or_cell_multipole": (ctypes.c_int, [dbl, p, p, p, dbl, p, p]),
+                "or_refresh_sizes": (ctypes.c_int, [i64, p, p, p, p, p, p, p, p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -197,8 +198,9 @@ def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None) -> T
     return t
 
 
-def walk(t: Tree, theta: float, eps: float, groups=None):
-    """§2.2 + §3.3 group walk (FP64).
+def walk(t: Tree, theta: float, eps: float, groups=None, mac: int = 0):
+    """§2.2 + §3.3 group walk (FP64).  ``mac`` 0: Eq. 1; 1: the minimal-distance
+    criterion (cell cube to group box farther than l/theta).
 
     Returns ``(acc, pot, stats)`` in SORTED order; ``acc``/``pot`` are only
     filled for bodies of the walked groups (NaN elsewhere).  ``stats`` is a
@@ -215,8 +217,8 @@ def walk(t: Tree, theta: float, eps: float, groups=None):
     amag = np.full(t.n, np.nan)
     lib.or_walk(len(grp), _p(grp), _p(t.gbeg), _p(t.gend), _p(t.gsys), _p(t.sys_root), t.C, _p(t.is_leaf),
                 _p(t.pbeg), _p(t.pend), _p(t.first_child), _p(t.n_children), _p(t.M), _p(t.com), _p(t.Q),
-                _p(t.size), _p(t.delta), t.n, _p(t.spos), _p(t.smass), float(theta), float(eps), _p(acc),
-                _p(pot), _p(raw), _p(amag))
+                _p(t.ctr), _p(t.size), _p(t.delta), t.n, _p(t.spos), _p(t.smass), float(theta), float(eps),
+                int(mac), _p(acc), _p(pot), _p(raw), _p(amag))
     stats = {
         "nc": raw[:, 0].copy(),
         "np": raw[:, 1].copy(),
@@ -228,10 +230,10 @@ def walk(t: Tree, theta: float, eps: float, groups=None):
     return acc, pot, stats
 
 
-def tree_forces(pos, mass, theta: float, eps: float, n_leaf: int = 16, n_crit: int = 64, offsets=None):
+def tree_forces(pos, mass, theta: float, eps: float, n_leaf: int = 16, n_crit: int = 64, offsets=None, mac: int = 0):
     """Build + walk all groups; accelerations and potentials in INPUT order."""
     t = build_tree(pos, mass, n_leaf, n_crit, offsets)
-    acc_s, pot_s, stats = walk(t, theta, eps)
+    acc_s, pot_s, stats = walk(t, theta, eps, mac=mac)
     acc = np.empty_like(acc_s)
     pot = np.empty_like(pot_s)
     acc[t.perm] = acc_s
@@ -299,3 +301,121 @@ def energy(vel, mass, pot):
 
 def momentum(vel, mass):
     return np.sum(mass[:, None] * vel, axis=0)
+
+
+# ---------------------------------------------------------------- block time-steps
+#
+# Reading (the paper motivates block time-steps -- §1, §2.2 "active" groups,
+# §4 moment refresh and rebuild on degradation -- but prints no scheme):
+#   * body i steps with dt_i = dt_max 2^-k_i, k_i in [0, k_max]; times are
+#     integer ticks of dt_max 2^-k_max;
+#   * the level wanted by a body is the smallest k with
+#     dt_max 2^-k <= eta sqrt(eps / |a|) (|a| = 0: level 0);
+#   * a block step advances to T = min_i (t_i + s_i), s_i = 2^(k_max - k_i);
+#     the bodies with t_i + s_i = T are active;
+#   * every body is predicted to T (x + v d + a d^2/2, d = (T - t_i) ticks),
+#     the tree is rebuilt at the predicted positions or refreshed on the old
+#     tree (refresh_tree), the groups holding an active body are walked, and
+#     the active bodies are corrected as in the shared-step leapfrog
+#     (v = v + a s + (a_new - a) s/2, x = predicted);
+#   * an active body then takes the wanted level if it is deeper, one level
+#     shallower if the wanted level is shallower and T is a multiple of the
+#     doubled step, else keeps its level.
+
+
+def refresh_tree(t: Tree, spos_new) -> Tree:
+    """The tree with new body positions (sorted order) and the same cells:
+    moments recomputed from the bodies, each cell's geometric centre kept and
+    its size grown to the smallest cube about that centre holding its bodies
+    or children (never below the built size)."""
+    import copy
+
+    lib = _load()
+    r = copy.copy(t)
+    r.spos = np.ascontiguousarray(spos_new, dtype=np.float64)
+    C = t.C
+    r.M, r.com, r.Q = np.zeros(C), np.zeros((C, 3)), np.zeros((C, 6))
+    r.ctr, r.size, r.delta = np.zeros((C, 3)), np.zeros(C), np.zeros(C)
+    lib.or_moments(C, _p(t.level), _p(t.pbeg), _p(t.pend), _p(t.csys), _p(r.spos), _p(t.smass), _p(t.sq),
+                   _p(t.frame), _p(r.M), _p(r.com), _p(r.Q), _p(r.ctr), _p(r.size), _p(r.delta))
+    lib.or_refresh_sizes(C, _p(t.is_leaf), _p(t.pbeg), _p(t.pend), _p(t.first_child), _p(t.n_children),
+                         _p(r.spos), _p(r.ctr), _p(r.size))
+    return r
+
+
+def block_level(acc, eps: float, eta: float, dt_max: float, k_max: int):
+    """Level wanted by each body: the smallest k >= 0 with
+    dt_max 2^-k <= eta sqrt(eps / |a|), clamped to k_max (FP64)."""
+    a = np.linalg.norm(np.asarray(acc, dtype=np.float64), axis=1)
+    r = dt_max * np.sqrt(a / eps) / eta  # need 2^k >= r
+    k = np.zeros(len(a), dtype=np.int64)
+    big = r > 1.0
+    m, e = np.frexp(r[big])  # r = m 2^e, m in [0.5, 1)
+    k[big] = np.where(m == 0.5, e - 1, e)
+    return np.minimum(k, k_max)
+
+
+class BlockState:
+    """Block time-step state, bodies in the caller's order."""
+
+    def __init__(self, x, v, m, dt_max, k_max, eta, n_leaf=16, n_crit=64):
+        self.x = np.array(x, dtype=np.float64)
+        self.v = np.array(v, dtype=np.float64)
+        self.m = np.array(m, dtype=np.float64)
+        self.dt_max, self.k_max, self.eta = float(dt_max), int(k_max), float(eta)
+        self.n_leaf, self.n_crit = n_leaf, n_crit
+        self.tick = self.dt_max / 2.0 ** self.k_max
+        n = len(self.m)
+        self.t = np.zeros(n, dtype=np.int64)
+        self.k = np.zeros(n, dtype=np.int64)
+        self.a = np.zeros((n, 3))
+        self.pot = np.zeros(n)
+        self.tree = None
+        self.T = 0
+
+
+def block_start(st: BlockState, theta: float, eps: float):
+    """Forces of every body at t = 0 and their first levels."""
+    a, pot, t, _ = tree_forces(st.x, st.m, theta, eps, st.n_leaf, st.n_crit)
+    st.a, st.pot, st.tree = a, pot, t
+    st.k = block_level(a, eps, st.eta, st.dt_max, st.k_max)
+    return st
+
+
+def block_step(st: BlockState, theta: float, eps: float, rebuild: bool = True, k_forced=None):
+    """One block step (see the reading above).  ``k_forced`` replaces the
+    levels the active bodies would take (for parity checks that must follow
+    another side's decisions).  Returns the boolean mask of active bodies."""
+    s = np.left_shift(np.int64(1), st.k_max - st.k)
+    T = int(np.min(st.t + s))
+    active = st.t + s == T
+    d = ((T - st.t) * st.tick)[:, None]
+    xp = st.x + st.v * d + 0.5 * st.a * d * d
+    if rebuild or st.tree is None:
+        tr = build_tree(xp, st.m, st.n_leaf, st.n_crit)
+    else:
+        tr = refresh_tree(st.tree, xp[st.tree.perm])
+    st.tree = tr
+    act_sorted = active[tr.perm]
+    groups = np.array([g for g in range(tr.G) if act_sorted[tr.gbeg[g]:tr.gend[g]].any()], dtype=np.int64)
+    acc_s, pot_s, _ = walk(tr, theta, eps, groups=groups)
+    a_new = np.empty_like(acc_s)
+    p_new = np.empty_like(pot_s)
+    a_new[tr.perm] = acc_s
+    p_new[tr.perm] = pot_s
+    ds = (s * st.tick)[:, None]
+    vp = st.v + st.a * ds
+    v_c = vp + 0.5 * (a_new - st.a) * ds
+    st.x[active] = xp[active]
+    st.v[active] = v_c[active]
+    st.a[active] = a_new[active]
+    st.pot[active] = p_new[active]
+    st.t[active] = T
+    want = block_level(a_new, eps, st.eta, st.dt_max, st.k_max) if k_forced is None else np.asarray(k_forced)
+    k_old = st.k.copy()
+    deeper = want > k_old
+    up_ok = (want < k_old) & (k_old > 0) & (T % (2 * s) == 0)
+    k_new = np.where(deeper, want, np.where(up_ok, k_old - 1, k_old))
+    st.k[active] = k_new[active]
+    st.T = T
+    return active

@@ -360,8 +360,11 @@ static void pp_force(const double *x, const double *xs, double m, double eps2, d
 }
 
 /* §2.2 + §3.3: breadth-first walk of every listed group.  The group's tight
- * bounding box is tested against each cell in the current level with Eq. 1;
- * accepted cells go to the cell list, opened nodes put their children on the
+ * bounding box is tested against each cell in the current level with Eq. 1
+ * (mac = 0: d > l/theta + delta, d from the cell's centre of mass to the box)
+ * or with the minimal-distance criterion the paper also implemented (§2.3,
+ * Salmon & Warren 1994; mac = 1: d > l/theta, d between the box and the
+ * cell's geometric cube, centre ctr, side l); accepted cells go to the cell list, opened nodes put their children on the
  * next level, opened leaves put their bodies on the particle list.  Every
  * body of the group then sums the cell list and the particle list (skipping
  * itself).  Bodies and outputs are in sorted order.
@@ -377,9 +380,9 @@ static void pp_force(const double *x, const double *xs, double m, double eps2, d
 int or_walk(int64_t ng, const int64_t *groups, const int64_t *gbeg, const int64_t *gend, const int32_t *gsys,
             const int64_t *sys_root, int64_t C, const int32_t *is_leaf, const int64_t *pbeg, const int64_t *pend,
             const int64_t *first_child, const int32_t *n_children, const double *M, const double *com,
-            const double *Q, const double *size, const double *delta, int64_t n, const double *spos,
-            const double *smass, double theta, double eps, double *acc, double *pot, int64_t *stats,
-            double *amag)
+            const double *Q, const double *ctr, const double *size, const double *delta, int64_t n,
+            const double *spos, const double *smass, double theta, double eps, int mac, double *acc, double *pot,
+            int64_t *stats, double *amag)
 {
     double eps2 = eps * eps;
 #pragma omp parallel
@@ -409,12 +412,19 @@ int or_walk(int64_t ng, const int64_t *groups, const int64_t *gbeg, const int64_
                     int64_t c = cur[t];
                     double d2 = 0.0;
                     for (int a = 0; a < 3; ++a) {
-                        double x = com[3 * c + a], e = 0.0;
-                        if (x < bmin[a]) e = bmin[a] - x;
-                        else if (x > bmax[a]) e = x - bmax[a];
+                        double e = 0.0;
+                        if (mac == 0) {  /* centre of mass to the group's box */
+                            double x = com[3 * c + a];
+                            if (x < bmin[a]) e = bmin[a] - x;
+                            else if (x > bmax[a]) e = x - bmax[a];
+                        } else {         /* the cell's cube to the group's box */
+                            double lo = ctr[3 * c + a] - 0.5 * size[c], hi = ctr[3 * c + a] + 0.5 * size[c];
+                            if (hi < bmin[a]) e = bmin[a] - hi;
+                            else if (lo > bmax[a]) e = lo - bmax[a];
+                        }
                         d2 += e * e;
                     }
-                    double r_open = size[c] / theta + delta[c];
+                    double r_open = (mac == 0) ? size[c] / theta + delta[c] : size[c] / theta;
                     double margin = fabs(sqrt(d2) - r_open) / r_open;
                     if (margin < min_margin) min_margin = margin;
                     if (d2 > r_open * r_open) {
@@ -514,5 +524,38 @@ int or_cell_multipole(double Mc, const double *cm, const double *Qc, const doubl
     pc_force(x, Mc, cm, Qc, eps * eps, a, &p);
     for (int b = 0; b < 3; ++b) acc[b] = a[b];
     *pot = p;
+    return 0;
+}
+
+/* ------------------------------------------- block time-steps: tree refresh */
+
+/* Cell sizes after a moment refresh on an unchanged tree (§4: between
+ * rebuilds only the moments of cells whose bodies moved are recomputed; the
+ * tree-cell size grows as bodies drift, which opens more cells).  Reading: a
+ * cell keeps its geometric centre ctr; its size becomes the side of the
+ * smallest cube about ctr that holds its bodies (a leaf) or its children's
+ * cubes (a node), never below the size it was built with.  size[] holds the
+ * built sizes on entry.  Children have larger indices than their parents
+ * ((level, key) order), so one pass from the last cell down suffices. */
+int or_refresh_sizes(int64_t C, const int32_t *is_leaf, const int64_t *pbeg, const int64_t *pend,
+                     const int64_t *first_child, const int32_t *n_children, const double *spos,
+                     const double *ctr, double *size)
+{
+    for (int64_t c = C - 1; c >= 0; --c) {
+        double l = size[c];
+        if (is_leaf[c]) {
+            for (int64_t i = pbeg[c]; i < pend[c]; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    double e = 2.0 * fabs(spos[3 * i + a] - ctr[3 * c + a]);
+                    if (e > l) l = e;
+                }
+        } else {
+            for (int32_t h = 0; h < n_children[c]; ++h) {
+                double e = 0.5 * size[c] + size[first_child[c] + h];
+                if (e > l) l = e;
+            }
+        }
+        size[c] = l;
+    }
     return 0;
 }

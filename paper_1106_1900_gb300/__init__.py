@@ -102,6 +102,7 @@ class bh_params(ctypes.Structure):
         ("list_capacity", ctypes.c_int32),
         ("pool_per_body", ctypes.c_int32),
         ("walk_split", ctypes.c_int32),
+        ("mac", ctypes.c_int32),
     ]
 
 

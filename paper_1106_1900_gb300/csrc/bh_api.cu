@@ -39,6 +39,7 @@ int validate_params(const bh_params *p) {
   if (p->walk_blocks_per_sm < 0 || p->walk_blocks_per_sm > 64) return BH_ERR_INVALID_ARG;
   if (p->list_capacity < 64 || p->pool_per_body < 1) return BH_ERR_INVALID_ARG;
   if (p->walk_split != 0 && p->walk_split != 1) return BH_ERR_INVALID_ARG;
+  if (p->mac != 0 && p->mac != 1) return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
 
@@ -256,7 +257,7 @@ int walk_phase(Ctx &c, float theta, float eps, bh::OutMode mode, float *acc, flo
   Phase ph(c, s, 5);
   cudaError_t e;
   if ((e = bh::launch_mac(c, theta, s))) return cu(e);
-  if ((e = bh::launch_walk(c, eps, mode, acc, pot, s))) return cu(e);
+  if ((e = bh::launch_walk(c, theta, eps, mode, acc, pot, s))) return cu(e);
   return BH_OK;
 }
 
@@ -314,6 +315,7 @@ int bh_default_params(bh_params *p) {
   p->list_capacity = 16384;
   p->pool_per_body = 768;
   p->walk_split = 0;
+  p->mac = 0;
   return BH_OK;
 }
 

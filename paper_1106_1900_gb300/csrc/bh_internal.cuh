@@ -138,7 +138,7 @@ cudaError_t launch_moments(Ctx &c, cudaStream_t s);
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s);
 // k_walk.cu
 enum OutMode { kOutCaller = 0, kOutSorted = 1 };
-cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s);
+cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s);
 int walk_smem_bytes(int warps);
 void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blocks_per_sm);
 // the fused walk unless the split form is asked for or the FP64 evaluation needs the pool

@@ -198,6 +198,32 @@ __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ coun
   }
 }
 
+// The minimal-distance criterion's record: the cell's geometric centre
+// (rounded to float) and its half side l/2 (exact); the walk tests the gap
+// between this cube and the group's box against l/theta = (l/2)(2/theta).
+template <bool FOREST>
+__global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ counts,
+                                                    const uint64_t *__restrict__ skey,
+                                                    const int32_t *__restrict__ offs, int S,
+                                                    const Frame *__restrict__ frame,
+                                                    const int32_t *__restrict__ c_level,
+                                                    const int32_t *__restrict__ c_pbeg, float4 *mac, uint32_t *queue,
+                                                    unsigned long long *pool_ctr, uint32_t *work_hist) {
+  const int C = counts[0];
+  if (blockIdx.x == 0) {  // the walk's group counters, list pool and cost histogram start empty
+    if (threadIdx.x == 0) {
+      queue[0] = 0;
+      queue[1] = 0;
+      pool_ctr[0] = 0;
+    }
+    for (int i = threadIdx.x; i < 2 * kCostBuckets; i += blockDim.x) work_hist[i] = 0;
+  }
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const Centre G = cell_centre<FOREST>(c_level[c] & 31, c_pbeg[c], skey, offs, S, frame);
+    mac[c] = make_float4(G.hi[0], G.hi[1], G.hi[2], 0.5f * G.l);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
@@ -216,7 +242,17 @@ cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
 
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s) {
   float inv = (theta > 0.f) ? 1.0f / theta : INFINITY;
-  k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
+  if (c.p.mac == 1) {
+    if (c.n_sys > 1)
+      k_mac_box<true><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.c_level,
+                                                       c.c_pbeg, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
+    else
+      k_mac_box<false><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.c_level,
+                                                        c.c_pbeg, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
+  } else {
+    k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr,
+                                           c.work_hist);
+  }
   c.launches++;
   return cudaGetLastError();
 }

@@ -61,6 +61,7 @@ constexpr float kFar = 1e18f;
 constexpr int kWarps = 4;  // warps per block of both kernels
 constexpr int kThreads = 32 * kWarps;
 constexpr int kEvalMinBlocks = 6;
+constexpr int kWalkMinBlocks = 6;  // the fused walk (7 measured slower at N_crit = 96)
 // Staging entries per warp: a 32-entry tile plus permanent nulls.  With k
 // phases a lane reads entries ph, ph + k, ... < cnt + ph, the last one at most
 // k ceil(32 / k) - 1, and k = 32 / h is one of 1, 2, 3, 4, 5, 6, 8, 10, 16,
@@ -180,6 +181,8 @@ struct TravArgs {
   unsigned long long *pool_ctr;
   int4 *g_list;  // per group: {pool offset, cells, bodies, estimated evaluation cost}
   uint32_t *work_hist;  // groups per cost bucket
+  int box_mac;           // 1: minimal-distance criterion (mac record = cube centre, half side)
+  float two_over_theta;  // its l/theta = (l/2) (2/theta)
   int n;
   uint32_t *queue;
   int32_t *g_npc;
@@ -287,11 +290,20 @@ __device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int l
         }
         if (base + 64 + lane < ncur) ci_nn = cstk[base + 64 + lane];
         const float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
-        const float ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
-        const float ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy), 0.f);
-        const float ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz), 0.f);
+        float ex, ey, ez, ro;
+        if (!A.box_mac) {  // Eq. 1: the centre of mass's distance to the box against r_open = m.w
+          ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
+          ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy), 0.f);
+          ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz), 0.f);
+          ro = m.w;
+        } else {  // minimal distance: the gap between the cube (half side m.w) and the box against l/theta
+          ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx) - m.w, 0.f);
+          ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy) - m.w, 0.f);
+          ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz) - m.w, 0.f);
+          ro = m.w * A.two_over_theta;
+        }
         const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        const bool accept = have && d2 > m.w * m.w;
+        const bool accept = have && d2 > ro * ro;
         const bool open = have && !accept;
         const bool leaf = lk.y < 0;
         // accepted cells -> cell list
@@ -896,7 +908,7 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
 // integer and load pipes, the evaluation bound by the FP32 pipe).  No list
 // pool, no copy; groups are taken largest first.
 template <int VAR, bool GUARD, int MODE>
-__global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_walk(TravArgs T, EvalArgs E) {
+__global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(TravArgs T, EvalArgs E) {
   extern __shared__ EvalSmem s_eval[];
   const int lane = threadIdx.x & 31;
   EvalSmem &S = s_eval[threadIdx.x >> 5];
@@ -1051,7 +1063,7 @@ void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blo
 
 int walk_block_warps() { return kWarps; }
 
-cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s) {
+cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s) {
   TravArgs t;
   t.part_hi = c.part_hi;
   t.part_lo = c.part_lo;
@@ -1070,6 +1082,8 @@ cudaError_t launch_walk(Ctx &c, float eps, OutMode mode, float *acc, float *pot,
   t.pool_ctr = c.pool_ctr;
   t.g_list = c.g_list;
   t.work_hist = c.work_hist;
+  t.box_mac = c.p.mac;
+  t.two_over_theta = (theta > 0.f) ? 2.0f / theta : INFINITY;
   t.n = (int)c.n;
   t.queue = c.walk_queue;
   t.g_npc = c.g_npc;

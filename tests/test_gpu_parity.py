@@ -41,7 +41,7 @@ def _run(bh, pos, mass, theta, eps, n_leaf=16, n_crit=64, offsets=None, **kw):
 
 def _full_parity(bh, pos, mass, theta, eps, n_leaf=16, n_crit=64, offsets=None, **kw):
     tc, acc, pot = _run(bh, pos, mass, theta, eps, n_leaf, n_crit, offsets, **kw)
-    acc_o, pot_o, t, st_o = oracle.tree_forces(pos, mass, theta, eps, n_leaf, n_crit, offsets)
+    acc_o, pot_o, t, st_o = oracle.tree_forces(pos, mass, theta, eps, n_leaf, n_crit, offsets, mac=kw.get("mac", 0))
     P.compare_tree(tc.tree(), t)
     if t.C:
         P.compare_moments(tc.moments(), t)
@@ -280,6 +280,19 @@ def test_fused_walk_equals_split_walk(cuda_lib, variant, n_crit):
     for k in ("nc", "np", "csum", "psum"):
         assert np.array_equal(g0[k], g1[k])
     assert (c0["pp"], c0["pc"]) == (c1["pp"], c1["pc"])
+
+
+@pytest.mark.parametrize("theta,split", [(0.5, 0), (0.75, 0), (0.5, 1)])
+def test_min_distance_mac_parity(cuda_lib, theta, split):
+    """§2.3's minimal-distance criterion against the oracle's: same lists
+    (up to near-tie flips), same forces within the tolerance."""
+    pos, _, m = ics.plummer(16384, 1)
+    _full_parity(cuda_lib, pos, m, theta, 0.01, mac=1, walk_split=split)
+
+
+def test_min_distance_mac_forest(cuda_lib):
+    pos, _, m, off = ics.ensemble(12, 3, n_min=200, n_max=3000)
+    _full_parity(cuda_lib, pos, m, 0.6, 0.01, offsets=off, mac=1)
 
 
 def test_forest_step_equals_systems(cuda_lib):

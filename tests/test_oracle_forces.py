@@ -154,6 +154,34 @@ def test_tree_error_vs_direct_by_theta():
     assert 1e-6 < med[1] < 1e-3  # quadrupole tree at theta = 0.5: ~1e-4
 
 
+# --------------------------------------- §2.3 minimal-distance criterion (mac = 1)
+@pytest.mark.parametrize("eps", [0.0, 0.01])
+def test_min_distance_theta_zero_is_direct_sum(eps):
+    pos, _, m = ics.plummer(1500, 12)
+    acc, pot, t, st = oracle.tree_forces(pos, m, theta=0.0, eps=eps, n_leaf=8, n_crit=32, mac=1)
+    assert np.all(st["nc"] == 0) and np.all(st["np"] == 1500)
+    ad, pd = oracle.direct(pos, m, eps)
+    assert np.allclose(acc, ad, rtol=1e-11, atol=1e-13 * np.abs(ad).max())
+    assert np.allclose(pot, pd, rtol=1e-12)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.75])
+def test_min_distance_is_more_accurate_and_costlier(theta):
+    # §2.3: the minimal-distance criterion gives smaller acceleration errors
+    # than Eq. 1 at the same theta, at the price of more interactions
+    pos, _, m = ics.plummer(8192, 7)
+    sub = ics.subsample(8192, 1024, 41)
+    ad, _ = oracle.direct(pos, m, 0.005, targets=sub)
+    rms, inter = [], []
+    for mac in (0, 1):
+        acc, _, t, st = oracle.tree_forces(pos, m, theta, 0.005, mac=mac)
+        e = np.linalg.norm(acc[sub] - ad, axis=1) / np.linalg.norm(ad, axis=1)
+        rms.append(np.sqrt(np.mean(e * e)))
+        inter.append(((t.gend - t.gbeg) * (st["nc"] + st["np"])).sum())
+    assert rms[1] < 0.95 * rms[0]
+    assert inter[1] > 1.1 * inter[0]
+
+
 def test_opening_margin_reported():
     pos, _, m = ics.plummer(4000, 14)
     _, _, _, st = oracle.tree_forces(pos, m, 0.5, 0.01)
