@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--untuned", action="store_true", help="use the paper's N_leaf = 16, N_crit = 64")
     ap.add_argument("--mac", type=int, default=0, choices=[0, 1],
                     help="opening criterion: 0 Eq. 1 (default), 1 minimal distance")
+    ap.add_argument("--block", action="store_true", help="add the block time-step measurement")
     ap.add_argument("--split", action="store_true",
                     help="split walk (lists through a pool, then a separate evaluation kernel)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
@@ -211,6 +212,62 @@ def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
             "sample": f"FP64 tree build of all {t.n} bodies ({t_build:.2f} s, charged pro rata) + walk of "
                       f"every {k}-th group ({len(groups)} groups, {bodies} bodies, {t_walk:.2f} s), "
                       f"theta={theta}, eps={eps}"}
+
+
+def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.02):
+    """Block time-steps on the same workload: one synchronised interval of
+    dt_max (rebuild at its start, moment refresh inside it), against stepping
+    every body with the smallest step any body used in it (what a shared step
+    needs for the same per-body accuracy), timed by one shared step."""
+    import torch
+
+    n = pos.shape[0]
+    tc = bh.TreeCode(n, device=dev.index, **params)
+    tc.set_state(pos, vel, mass)
+    tc.block_start(dt_max, k_max, eta, theta, eps)
+    sync = 2 ** k_max
+    # one warm interval, then the timed one
+    for rep in range(2):
+        t0 = tc.block_info()["tick"]
+        torch.cuda.synchronize()
+        start = time.perf_counter()
+        steps = updates = rebuilds = 0
+        deepest = 0
+        while True:
+            tick = tc.block_info()["tick"]
+            if tick >= t0 + sync:
+                break
+            rebuild = tick % sync == 0
+            tc.block_step(theta, eps, rebuild=rebuild)
+            info = tc.block_info()
+            steps += 1
+            updates += info["active"]
+            rebuilds += int(rebuild)
+            deepest = max(deepest, info["deepest"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - start
+    tc.check()
+    # a shared step of the same system (graph replay), for the comparison
+    ts = bh.TreeCode(n, device=dev.index, **params)
+    ts.set_state(pos, vel, mass)
+    for _ in range(3):
+        ts.step(dt_max / 2 ** deepest, theta, eps, graph=True)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        ts.step(dt_max / 2 ** deepest, theta, eps, graph=True)
+    b.record()
+    torch.cuda.synchronize()
+    shared_ms = a.elapsed_time(b) / 5
+    shared_interval_s = shared_ms * 1e-3 * 2 ** deepest
+    return {"what": f"block time-steps, dt_max = 1/{round(1 / dt_max)}, k_max = {k_max}, eta = {eta}: one "
+                    "synchronised dt_max interval (host-driven block steps, rebuild at its start, moment refresh "
+                    "inside) against shared steps of the smallest step used",
+            "block_steps": steps, "rebuilds": rebuilds, "deepest_level": deepest,
+            "body_updates": updates, "updates_per_s": updates / wall, "interval_s": wall,
+            "shared_step_ms": shared_ms, "shared_interval_s": shared_interval_s,
+            "speedup_vs_shared": shared_interval_s / wall}
 
 
 def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
@@ -450,6 +507,9 @@ def main():
     ens = None
     if not args.no_ensemble and args.workload == "plummer":
         ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=3, warmup=2)
+    blk = None
+    if args.block and args.workload == "plummer":
+        blk = block_compare(bh, dev, P, V, M, args.theta, EPS, kw)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pos, m, args.theta, eps)
@@ -488,6 +548,7 @@ def main():
         "clocks": clocks,
         "cpu_baseline": cpu,
         "ensemble": ens,
+        "block": blk,
         "wall_s_timed": wall1 - wall0,
     }
     print(json.dumps(out), flush=True)

@@ -157,6 +157,40 @@ int bh_step(bh_ctx *ctx, double dt, float theta, float eps, void *stream);
  * call then launches the graph on `stream`. */
 int bh_step_graph(bh_ctx *ctx, double dt, float theta, float eps, void *stream);
 
+/* ---- Block time-steps (the paper's motivation for an all-GPU tree code:
+ * §1, the "active" groups of §2.2, moment refresh and rebuild of §4).  No
+ * scheme is printed; the one built here: body i steps with dt_max 2^-k_i,
+ * k_i in 0..k_max, on integer ticks of dt_max 2^-k_max; the level wanted is
+ * the smallest k with dt_max 2^-k <= eta sqrt(eps / |a_i|).  A block step
+ * advances to the earliest time T a body is due, predicts every body to T
+ * (the bh_step predictor), rebuilds the tree at the predicted positions or
+ * refreshes its moments on the unchanged tree (a cell keeps its geometric
+ * centre and grows to the smallest cube about it holding its bodies or
+ * children), walks only the groups holding a due body, and corrects the due
+ * bodies (the bh_step corrector); a due body then takes a deeper level at
+ * once, or one level shallower when T is a multiple of the doubled step.
+ * With k_max = 0 a block step is a bh_step with dt = dt_max, bit for bit. */
+
+/* Starts block time-stepping on the loaded state (bh_set_state): forces of
+ * every body at t = 0, first levels, every body at tick 0.  eps > 0,
+ * 0 <= k_max <= 40, dt_max > 0, eta > 0.  The state is left in the tree's
+ * body order; bh_get_state still returns the caller's order. */
+int bh_block_start(bh_ctx *ctx, double dt_max, int32_t k_max, double eta, float theta, float eps, void *stream);
+
+/* One block step.  rebuild != 0 builds the tree anew at the predicted
+ * positions; 0 refreshes the moments on the last tree (the first step after
+ * bh_block_start may refresh).  BH_ERR_STATE without bh_block_start; a
+ * bh_step, bh_set_state or bh_build ends block time-stepping. */
+int bh_block_step(bh_ctx *ctx, float theta, float eps, int32_t rebuild, void *stream);
+
+/* out[0] block time of the last step (ticks), out[1] bodies due at it,
+ * out[2] groups walked, out[3] deepest level held after it.  Synchronises. */
+int bh_block_info(bh_ctx *ctx, int64_t out[4], void *stream);
+
+/* Each body's level (int32 [n]) and the tick of its last update (int64 [n]),
+ * device buffers in the caller's order; either may be NULL. */
+int bh_block_levels(bh_ctx *ctx, int32_t *level_dev, int64_t *tick_dev, void *stream);
+
 /* Energies and momentum of the current state (FP64, synchronises):
  * out[0] kinetic, out[1] potential = 1/2 sum m phi, out[2..4] momentum.
  * The potentials are those of the last force evaluation. */

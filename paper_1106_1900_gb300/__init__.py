@@ -127,6 +127,11 @@ _SIG = {
     "bh_step": [ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_float, ctypes.c_void_p],
     "bh_step_graph": [ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_float, ctypes.c_void_p],
     "bh_diagnostics": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "bh_block_start": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_float,
+                       ctypes.c_float, ctypes.c_void_p],
+    "bh_block_step": [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_void_p],
+    "bh_block_info": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "bh_block_levels": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "bh_status": [ctypes.c_void_p, ctypes.c_void_p],
     "bh_get_counts": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "bh_reset_counters": [ctypes.c_void_p, ctypes.c_void_p],
@@ -304,6 +309,7 @@ class TreeCode:
             optr, ns = None, 1
         _check(self.lib.bh_set_state(self.ctx, _ptr(pos), _ptr(vel), _ptr(mass), n, optr, ns, _stream(stream)),
                "bh_set_state")
+        self.n_state = n
 
     def get_state(self, pos=None, vel=None, acc=None, pot=None, stream=None):
         _check(self.lib.bh_get_state(self.ctx, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(pot), _stream(stream)),
@@ -317,6 +323,35 @@ class TreeCode:
         out = (ctypes.c_double * 5)()
         _check(self.lib.bh_diagnostics(self.ctx, out, _stream(stream)), "bh_diagnostics")
         return {"ekin": out[0], "epot": out[1], "mom": (out[2], out[3], out[4])}
+
+    # ---- block time-steps
+    def block_start(self, dt_max: float, k_max: int, eta: float, theta: float, eps: float, stream=None):
+        """Forces at t = 0 and first levels on the loaded state (bh_block_start)."""
+        _check(self.lib.bh_block_start(self.ctx, float(dt_max), int(k_max), float(eta), float(theta), float(eps),
+                                       _stream(stream)), "bh_block_start")
+        self.blk = (float(dt_max), int(k_max))
+
+    def block_step(self, theta: float, eps: float, rebuild: bool = True, stream=None):
+        """One block step: rebuild the tree or refresh its moments (bh_block_step)."""
+        _check(self.lib.bh_block_step(self.ctx, float(theta), float(eps), int(bool(rebuild)), _stream(stream)),
+               "bh_block_step")
+
+    def block_info(self, stream=None) -> dict:
+        out = (ctypes.c_int64 * 4)()
+        _check(self.lib.bh_block_info(self.ctx, out, _stream(stream)), "bh_block_info")
+        dt_max, k_max = self.blk
+        return {"tick": out[0], "time": out[0] * dt_max / 2.0 ** k_max, "active": out[1], "groups": out[2],
+                "deepest": out[3]}
+
+    def block_levels(self, stream=None):
+        """(levels int32 [n], ticks int64 [n]) in the caller's order, on the device."""
+        import torch
+
+        lv = torch.empty(self.n_state, dtype=torch.int32, device=f"cuda:{self.device}")
+        tk = torch.empty(self.n_state, dtype=torch.int64, device=f"cuda:{self.device}")
+        _check(self.lib.bh_block_levels(self.ctx, ctypes.c_void_p(lv.data_ptr()), ctypes.c_void_p(tk.data_ptr()),
+                                        _stream(stream)), "bh_block_levels")
+        return lv, tk
 
     # ---- status and exports
     def status(self, stream=None) -> int:

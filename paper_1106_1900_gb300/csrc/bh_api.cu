@@ -119,6 +119,8 @@ void carve(Ctx &c, char *base, size_t *total) {
     c.st_m[b] = k.take<double>(N);
     c.st_a[b] = k.take<float4>(N);
     c.st_id[b] = k.take<int32_t>(N);
+    c.st_t[b] = k.take<int64_t>(N);
+    c.st_k[b] = k.take<int32_t>(N);
   }
   c.h_pos = k.take<double>(3 * N);
   c.h_mass = k.take<double>(N);
@@ -156,6 +158,10 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.g_order = k.take<int32_t>(N);
   c.walk_queue = k.take<uint32_t>(2);
   c.d_counts = k.take<int32_t>(4);
+  c.pred_x = k.take<double>(3 * N);
+  c.pred_s = k.take<double>(3 * N);
+  c.g_active = k.take<uint8_t>(N);
+  c.d_block = k.take<unsigned long long>(4);
   c.d_totals = k.take<unsigned long long>(4);
   c.d_status = k.take<int32_t>(1);
   c.d_diag = k.take<double>(5 + 256 * 5);
@@ -224,8 +230,11 @@ int upload_offsets(Ctx &c, int64_t n, const int64_t *offs, int32_t S, cudaStream
   return cu(cudaStreamSynchronize(s));
 }
 
-// keys, sort, cells, moments from positions/masses in [n][3] / [n] layout
-int build_pipeline(Ctx &c, const double *pos, const double *mass, bool state_path, cudaStream_t s) {
+// keys, sort, cells, moments from positions/masses in [n][3] / [n] layout;
+// the move permutes nothing (a plain build), the state, or the state with its
+// block time-step ticks and levels (the tree's bodies then from pos)
+enum Move { kMovePlain = 0, kMoveState = 1, kMoveBlock = 2 };
+int build_pipeline(Ctx &c, const double *pos, const double *mass, Move move, cudaStream_t s) {
   cudaError_t e;
   {
     Phase ph(c, s, 0);
@@ -238,7 +247,8 @@ int build_pipeline(Ctx &c, const double *pos, const double *mass, bool state_pat
   }
   {
     Phase ph(c, s, 2);
-    if (state_path) e = bh::launch_move_state(c, s);
+    if (move == kMoveBlock) e = bh::launch_move_block(c, s);
+    else if (move == kMoveState) e = bh::launch_move_state(c, s);
     else e = bh::launch_move(c, pos, mass, s);
     if (e) return cu(e);
   }
@@ -253,11 +263,12 @@ int build_pipeline(Ctx &c, const double *pos, const double *mass, bool state_pat
   return BH_OK;
 }
 
-int walk_phase(Ctx &c, float theta, float eps, bh::OutMode mode, float *acc, float *pot, cudaStream_t s) {
+int walk_phase(Ctx &c, float theta, float eps, bh::OutMode mode, float *acc, float *pot, cudaStream_t s,
+               const uint8_t *g_active = nullptr) {
   Phase ph(c, s, 5);
   cudaError_t e;
   if ((e = bh::launch_mac(c, theta, s))) return cu(e);
-  if ((e = bh::launch_walk(c, theta, eps, mode, acc, pot, s))) return cu(e);
+  if ((e = bh::launch_walk(c, theta, eps, mode, acc, pot, s, g_active))) return cu(e);
   return BH_OK;
 }
 
@@ -275,7 +286,7 @@ int step_impl(Ctx &c, double dt, float theta, float eps, bool init, cudaStream_t
     if ((e = bh::launch_predict(c, dt, s))) return cu(e);
   }
   const int a = c.state_cur;
-  int rc = build_pipeline(c, c.st_x[a], c.st_m[a], true, s);
+  int rc = build_pipeline(c, c.st_x[a], c.st_m[a], kMoveState, s);
   if (rc) return rc;
   rc = walk_phase(c, theta, eps, bh::kOutSorted, nullptr, nullptr, s);
   if (rc) return rc;
@@ -404,13 +415,14 @@ static int build_common(bh_ctx *ctx, const double *pos, const double *mass, int6
   c.n = n;
   c.built = c.forces = false;
   c.have_state = c.have_acc = false;
+  c.block_on = c.block_tree = false;
   drop_graphs(c);
   for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
   if (c.profiling) cudaEventRecord(c.ev[7][0], s);
   if (n == 0) {
     rc = cu(cudaMemsetAsync(c.d_counts, 0, 4 * sizeof(int32_t), s));
   } else {
-    rc = build_pipeline(c, pos, mass, false, s);
+    rc = build_pipeline(c, pos, mass, kMovePlain, s);
   }
   if (c.profiling) {
     cudaEventRecord(c.ev[7][1], s);
@@ -496,6 +508,7 @@ int bh_set_state(bh_ctx *ctx, const double *pos, const double *vel, const double
   c.state_cur = 0;
   drop_graphs(c);
   c.built = c.forces = false;
+  c.block_on = c.block_tree = false;
   if (n > 0) {
     cudaError_t e = bh::launch_load_state(c, pos, vel, mass, s);
     if (e) return cu(e);
@@ -525,6 +538,7 @@ int bh_step(bh_ctx *ctx, double dt, float theta, float eps, void *stream) {
   if (!std::isfinite(dt)) return BH_ERR_INVALID_ARG;
   DeviceGuard g(c.device);
   cudaStream_t s = (cudaStream_t)stream;
+  c.block_on = c.block_tree = false;  // a shared step moves every body by dt
   for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
   if (c.profiling) cudaEventRecord(c.ev[7][0], s);
   if (!c.have_acc) {
@@ -550,6 +564,7 @@ int bh_step_graph(bh_ctx *ctx, double dt, float theta, float eps, void *stream) 
   if (!std::isfinite(dt)) return BH_ERR_INVALID_ARG;
   DeviceGuard g(c.device);
   cudaStream_t s = (cudaStream_t)stream;
+  c.block_on = c.block_tree = false;  // a shared step moves every body by dt
   if (!c.have_acc) {
     rc = step_impl(c, 0.0, theta, eps, true, s);
     if (rc) return rc;
@@ -590,6 +605,114 @@ int bh_step_graph(bh_ctx *ctx, double dt, float theta, float eps, void *stream) 
   }
   c.launches += c.graph_launches[par];
   return cu(cudaGraphLaunch(c.graph_exec[par], s));
+}
+
+int bh_block_start(bh_ctx *ctx, double dt_max, int32_t k_max, double eta, float theta, float eps, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.have_state) return BH_ERR_STATE;
+  rc = check_theta_eps(theta, eps);
+  if (rc) return rc;
+  if (!(eps > 0.f) || !(dt_max > 0.0) || !std::isfinite(dt_max) || !(eta > 0.0) || !std::isfinite(eta) ||
+      k_max < 0 || k_max > 40)
+    return BH_ERR_INVALID_ARG;
+  DeviceGuard g(c.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c.block_on = c.block_tree = false;
+  c.blk_dt_max = dt_max;
+  c.blk_kmax = k_max;
+  c.blk_eta = eta;
+  c.blk_tick = std::ldexp(dt_max, -k_max);
+  if (c.n == 0) {
+    c.block_on = true;
+    return BH_OK;
+  }
+  // forces at t = 0 for every body (the state is left in the tree's body order)
+  rc = step_impl(c, 0.0, theta, eps, true, s);
+  if (rc) return rc;
+  c.have_acc = true;
+  if ((rc = cu(bh::launch_block_levels(c, (double)eps, s)))) return rc;
+  c.block_on = c.block_tree = true;
+  return BH_OK;
+}
+
+int bh_block_step(bh_ctx *ctx, float theta, float eps, int32_t rebuild, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.block_on) return BH_ERR_STATE;
+  rc = check_theta_eps(theta, eps);
+  if (rc) return rc;
+  if (!(eps > 0.f)) return BH_ERR_INVALID_ARG;
+  if (c.n == 0) return BH_OK;
+  DeviceGuard g(c.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  drop_graphs(c);
+  for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
+  if (c.profiling) cudaEventRecord(c.ev[7][0], s);
+  const bool full = rebuild || !c.block_tree;
+  cudaError_t e;
+  {
+    Phase ph(c, s, 6);
+    if ((e = bh::launch_block_predict(c, s))) return cu(e);
+  }
+  if (full) {
+    rc = build_pipeline(c, c.pred_x, c.st_m[c.state_cur], kMoveBlock, s);
+    if (rc) return rc;
+  } else {
+    {
+      Phase ph(c, s, 2);
+      if ((e = bh::launch_block_parts(c, s))) return cu(e);
+    }
+    Phase ph(c, s, 4);
+    if ((e = bh::launch_moments_refresh(c, s))) return cu(e);
+  }
+  if ((e = bh::launch_group_active(c, s))) return cu(e);
+  rc = walk_phase(c, theta, eps, bh::kOutSorted, nullptr, nullptr, s, c.g_active);
+  if (rc) return rc;
+  {
+    Phase ph(c, s, 6);
+    if ((e = bh::launch_block_correct(c, (double)eps, full, s))) return cu(e);
+  }
+  if (c.profiling) {
+    cudaEventRecord(c.ev[7][1], s);
+    c.phase_rec[7] = true;
+  }
+  c.built = c.forces = c.block_tree = true;
+  return BH_OK;
+}
+
+int bh_block_info(bh_ctx *ctx, int64_t out[4], void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!out) return BH_ERR_INVALID_ARG;
+  if (!c.block_on) return BH_ERR_STATE;
+  for (int q = 0; q < 4; ++q) out[q] = 0;
+  if (c.n == 0) return BH_OK;
+  DeviceGuard g(c.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long b[4];
+  int32_t cnt[4];
+  if ((rc = cu(cudaMemcpyAsync(b, c.d_block, sizeof(b), cudaMemcpyDeviceToHost, s)))) return rc;
+  if ((rc = cu(cudaMemcpyAsync(cnt, c.d_counts, sizeof(cnt), cudaMemcpyDeviceToHost, s)))) return rc;
+  if ((rc = cu(cudaStreamSynchronize(s)))) return rc;
+  out[0] = (int64_t)b[0];
+  out[1] = (int64_t)b[1];
+  out[2] = (int64_t)cnt[3];
+  out[3] = (int64_t)b[2];
+  return BH_OK;
+}
+
+int bh_block_levels(bh_ctx *ctx, int32_t *level, int64_t *tick, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.block_on) return BH_ERR_STATE;
+  if (c.n == 0) return BH_OK;
+  DeviceGuard g(c.device);
+  return cu(bh::launch_block_get(c, level, tick, (cudaStream_t)stream));
 }
 
 int bh_diagnostics(bh_ctx *ctx, double out[5], void *stream) {

@@ -46,6 +46,11 @@ struct Ctx {
   bool have_state = false;  // bh_set_state done
   bool have_acc = false;    // a_old valid for the state
   int state_cur = 0;        // which state buffer (0/1) is current
+  // block time-steps: levels k (steps dt_max 2^-k) on integer ticks of dt_max 2^-k_max
+  bool block_on = false;    // bh_block_start done since the state was loaded
+  bool block_tree = false;  // the tree matches the state's body order (a refresh is possible)
+  double blk_dt_max = 0.0, blk_tick = 0.0, blk_eta = 0.0;
+  int blk_kmax = 0;
   int64_t host_offsets_sig = -1;
 
   // ---- device buffers (carved from the workspace)
@@ -65,6 +70,12 @@ struct Ctx {
   double *st_x[2], *st_v[2], *st_m[2];
   float4 *st_a[2];
   int32_t *st_id[2];
+  int64_t *st_t[2];              // block time-steps: tick of the body's last update
+  int32_t *st_k[2];              // block time-steps: the body's level
+  double *pred_x;                // [n][3] positions predicted to the block time (state order)
+  double *pred_s;                // [n][3] the same after a rebuild's permutation (sorted order)
+  uint8_t *g_active;             // [G] group holds a body due at the block time
+  unsigned long long *d_block;   // [0] block time (ticks), [1] active bodies, [2] deepest level
   double *h_pos, *h_mass;        // staging for bh_forces_host
   float *h_acc, *h_pot;
   // per warp of the level pass
@@ -100,7 +111,7 @@ struct Ctx {
   int32_t *g_order;              // [G] groups in order of decreasing estimated cost
   uint32_t *walk_queue;          // [2] traversal, evaluation
   // scalars
-  int32_t *d_counts;             // [0] C, [1] G, [2] max level
+  int32_t *d_counts;             // [0] C, [1] G, [2] max level, [3] groups in the walk's order
   unsigned long long *d_totals;  // [0] pp, [1] pc, [2] walk launches
   int32_t *d_status;             // [1]
   double *d_diag;                // [5 + blocks*5]
@@ -135,10 +146,12 @@ cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, ui
 int64_t scan_blocks_for(int64_t n);
 // k_moments.cu
 cudaError_t launch_moments(Ctx &c, cudaStream_t s);
+cudaError_t launch_moments_refresh(Ctx &c, cudaStream_t s);
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s);
 // k_walk.cu
 enum OutMode { kOutCaller = 0, kOutSorted = 1 };
-cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s);
+cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s,
+                        const uint8_t *g_active = nullptr);
 int walk_smem_bytes(int warps);
 void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blocks_per_sm);
 // the fused walk unless the split form is asked for or the FP64 evaluation needs the pool
@@ -146,6 +159,14 @@ inline bool walk_is_fused(const bh_params &p) { return p.walk_split == 0 && p.wa
 int walk_block_warps();
 cudaError_t walk_init_attrs(int smem);
 cudaError_t build_init_attrs();
+// k_block.cu
+cudaError_t launch_block_levels(Ctx &c, double eps, cudaStream_t s);
+cudaError_t launch_block_predict(Ctx &c, cudaStream_t s);
+cudaError_t launch_move_block(Ctx &c, cudaStream_t s);
+cudaError_t launch_block_parts(Ctx &c, cudaStream_t s);
+cudaError_t launch_group_active(Ctx &c, cudaStream_t s);
+cudaError_t launch_block_correct(Ctx &c, double eps, bool rebuilt, cudaStream_t s);
+cudaError_t launch_block_get(Ctx &c, int32_t *level, int64_t *tick, cudaStream_t s);
 // k_integrate.cu
 cudaError_t launch_predict(Ctx &c, double dt, cudaStream_t s);
 cudaError_t launch_correct(Ctx &c, double dt, cudaStream_t s);

@@ -54,14 +54,14 @@ __device__ __forceinline__ Centre cell_centre(int k, int i, const uint64_t *__re
 }
 
 __device__ __forceinline__ void write_cell(float4 *mom, int c, const Centre &C, float M, const float cm[3],
-                                           const float Q[6]) {
+                                           const float Q[6], float l) {
   float hi[3], lo[3];
   for (int a = 0; a < 3; ++a) split2(__dadd_rn(C.c[a], (double)cm[a]), hi[a], lo[a]);
   float delta = sqrtf(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]);
   mom[4 * (size_t)c + 0] = make_float4(hi[0], hi[1], hi[2], M);
   mom[4 * (size_t)c + 1] = make_float4(lo[0], lo[1], lo[2], delta);
   mom[4 * (size_t)c + 2] = make_float4(Q[0], Q[1], Q[2], Q[3]);
-  mom[4 * (size_t)c + 3] = make_float4(Q[4], Q[5], C.l, 0.f);
+  mom[4 * (size_t)c + 3] = make_float4(Q[4], Q[5], l, 0.f);
 }
 
 __device__ __forceinline__ void add_point_quad(float Q[6], float m, float dx, float dy, float dz) {
@@ -74,7 +74,11 @@ __device__ __forceinline__ void add_point_quad(float Q[6], float m, float dx, fl
   Q[5] += m * 3.f * dy * dz;
 }
 
-template <bool FOREST>
+// REFRESH: the tree is unchanged but its bodies moved (block time-steps); a
+// cell keeps its geometric centre and its size grows to the smallest cube
+// about that centre holding its bodies (a leaf) or its children's cubes (a
+// node, l/2 + the largest child side), never below its built size.
+template <bool FOREST, bool REFRESH>
 __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__ skey,
                                                     const int32_t *__restrict__ offs, int S,
                                                     const Frame *__restrict__ frame,
@@ -95,12 +99,13 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
     {
       const int k = lv & 31, b = c_pbeg[c], e = c_pend[c];
       Centre G = cell_centre<FOREST>(k, b, skey, offs, S, frame);
-      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, ext = 0.f;
       for (int i = b; i < e; ++i) {
         float4 h = part_hi[i], l = part_lo[i];
         float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]);
         float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]);
         float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]);
+        if (REFRESH) ext = fmaxf(ext, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
         M += h.w;
         sx += h.w * dx;
         sy += h.w * dy;
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
         float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]) - cm[2];
         add_point_quad(Q, h.w, dx, dy, dz);
       }
-      write_cell(mom, c, G, M, cm, Q);
+      write_cell(mom, c, G, M, cm, Q, REFRESH ? fmaxf(G.l, 2.f * ext) : G.l);
     }
     // ---- climb while this thread is the last child to arrive
     int cur = c;
@@ -135,10 +140,11 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
       const int k = c_level[p] & 31;
       Centre G = cell_centre<FOREST>(k, c_pbeg[p], skey, offs, S, frame);
       const int f = c_first[p];
-      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, lch = 0.f;
       for (uint32_t j = 0; j < nch; ++j) {
         float4 a = __ldcg(&mom[4 * (size_t)(f + j)]);
         float4 b = __ldcg(&mom[4 * (size_t)(f + j) + 1]);
+        if (REFRESH) lch = fmaxf(lch, __ldcg(&mom[4 * (size_t)(f + j) + 3]).z);
         float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]);
         float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]);
         float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]);
@@ -170,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
         Q[5] += q1.y;
         add_point_quad(Q, a.w, dx, dy, dz);
       }
-      write_cell(mom, p, G, M, cm, Q);
+      write_cell(mom, p, G, M, cm, Q, REFRESH ? fmaxf(G.l, fmaf(0.5f, G.l, lch)) : G.l);
       cur = p;
     }
   }
@@ -196,6 +202,13 @@ __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ coun
     float l = mom[4 * (size_t)c + 3].z;
     mac[c] = make_float4(a.x, a.y, a.z, fmaf(l, inv_theta, delta));
   }
+}
+
+// Arrival counters of the bottom-up pass back to zero (a moment refresh on an
+// unchanged tree; a build clears them while it emits the cells).
+__global__ void __launch_bounds__(kBlock) k_clear_counters(const int32_t *__restrict__ counts, uint32_t *c_ctr) {
+  const int C = counts[0];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) c_ctr[c] = 0;
 }
 
 // The minimal-distance criterion's record: the cell's geometric centre
@@ -226,16 +239,31 @@ __global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ 
 
 }  // namespace
 
-cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
+template <bool REFRESH>
+static void moments_launch(Ctx &c, cudaStream_t s) {
   const int nb = c.num_sms * 8;
   if (c.n_sys > 1)
-    k_moments<true><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level, c.c_pbeg,
-                                          c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr, c.part_hi, c.part_lo,
-                                          c.c_mom);
+    k_moments<true, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level,
+                                                   c.c_pbeg, c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr,
+                                                   c.part_hi, c.part_lo, c.c_mom);
   else
-    k_moments<false><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level, c.c_pbeg,
-                                           c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr, c.part_hi,
-                                           c.part_lo, c.c_mom);
+    k_moments<false, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level,
+                                                    c.c_pbeg, c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr,
+                                                    c.part_hi, c.part_lo, c.c_mom);
+}
+
+cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
+  moments_launch<false>(c, s);
+  c.launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_refresh(Ctx &c, cudaStream_t s) {
+  k_clear_counters<<<c.num_sms * 4, kBlock, 0, s>>>(c.d_counts, c.c_ctr);
+  cudaError_t e = cudaGetLastError();
+  c.launches++;
+  if (e) return e;
+  moments_launch<true>(c, s);
   c.launches++;
   return cudaGetLastError();
 }

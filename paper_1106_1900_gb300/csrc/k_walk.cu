@@ -463,12 +463,14 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
 // known before its walk; the body count is the best early estimate).
 __device__ __forceinline__ int size_bucket(int n) { return min(max(n, 0), kCostBuckets - 1); }
 
-// Histogram of the group sizes (fused walk).
+// Histogram of the group sizes (fused walk); with a flag array, of the
+// flagged (active) groups only.
 __global__ void __launch_bounds__(256) k_size_hist(const int32_t *__restrict__ counts,
-                                                    const int32_t *__restrict__ g_beg, uint32_t *work_hist) {
+                                                    const int32_t *__restrict__ g_beg,
+                                                    const uint8_t *__restrict__ g_active, uint32_t *work_hist) {
   const int G = counts[1];
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
-    atomicAdd(&work_hist[size_bucket(g_beg[g + 1] - g_beg[g])], 1u);
+    if (!g_active || g_active[g]) atomicAdd(&work_hist[size_bucket(g_beg[g + 1] - g_beg[g])], 1u);
 }
 
 // Places the groups in order of decreasing estimated cost: the groups of
@@ -477,9 +479,9 @@ __global__ void __launch_bounds__(256) k_size_hist(const int32_t *__restrict__ c
 // Every block recomputes the bucket offsets from the histogram; appends are
 // aggregated per warp over lanes of equal bucket.
 template <bool BY_SIZE>
-__global__ void __launch_bounds__(kCostBuckets) k_order(const int32_t *__restrict__ counts,
-                                                         const int4 *__restrict__ g_list,
-                                                         const int32_t *__restrict__ g_beg, uint32_t *work_hist,
+__global__ void __launch_bounds__(kCostBuckets) k_order(int32_t *counts, const int4 *__restrict__ g_list,
+                                                         const int32_t *__restrict__ g_beg,
+                                                         const uint8_t *__restrict__ g_active, uint32_t *work_hist,
                                                          int32_t *order) {
   __shared__ uint32_t s_start[kCostBuckets];
   __shared__ uint32_t s_warp[kCostBuckets / 32];
@@ -496,13 +498,15 @@ __global__ void __launch_bounds__(kCostBuckets) k_order(const int32_t *__restric
   uint32_t off = 0;
   for (int i = 0; i < w; ++i) off += s_warp[i];
   s_start[kCostBuckets - 1 - t] = off + x - v;
+  if (blockIdx.x == 0 && t == kCostBuckets - 1) counts[3] = (int32_t)(off + x);  // groups placed: the walk's count
   __syncthreads();
   const int G = counts[1];
   uint32_t *fill = work_hist + kCostBuckets;
   const unsigned lt = lanemask_lt();
   for (int base = blockIdx.x * blockDim.x; base < G; base += gridDim.x * blockDim.x) {
     const int g = base + t;
-    const int b = (g >= G) ? -1 : BY_SIZE ? size_bucket(g_beg[g + 1] - g_beg[g]) : cost_bucket(g_list[g].w);
+    const int b = (g >= G || (g_active && !g_active[g])) ? -1
+                  : BY_SIZE ? size_bucket(g_beg[g + 1] - g_beg[g]) : cost_bucket(g_list[g].w);
     const unsigned peers = __match_any_sync(kFull, b);
     const int leader = __ffs(peers) - 1;
     uint32_t first = 0;
@@ -533,7 +537,7 @@ struct EvalArgs {
   const int32_t *__restrict__ g_beg;
   const int4 *__restrict__ g_list;
   const uint32_t *__restrict__ pool;
-  const int32_t *__restrict__ counts;
+  const int32_t *__restrict__ counts;  // [1] groups, [3] groups in the order
   const int32_t *__restrict__ order;  // groups, most expensive first
   float eps2;
   uint32_t *queue;
@@ -886,12 +890,12 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
   const int lane = threadIdx.x & 31;
   EvalSmem &S = s_eval[threadIdx.x >> 5];
   init_stage(S, lane);
-  const int G = A.counts[1];
+  const int G = A.counts[1], NQ = A.counts[3];  // groups; groups in the order
   while (true) {
     int q = 0;
     if (lane == 0) q = (int)atomicAdd(A.queue, 1u);
     q = __shfl_sync(kFull, q, 0);
-    if (q >= G) break;
+    if (q >= NQ) break;
     const int g = A.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
     const int4 L = A.g_list[g];
@@ -919,12 +923,12 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(TravArgs T, E
   int *cl = T.scratch + gw * 2 * (size_t)T.list_cap;
   int *pl = cl + T.list_cap;
   const unsigned lt = lanemask_lt();
-  const int G = T.counts[1];
+  const int G = T.counts[1], NQ = T.counts[3];  // groups; groups in the order (the active ones)
   while (true) {
     int q = 0;
     if (lane == 0) q = (int)atomicAdd(E.queue, 1u);
     q = __shfl_sync(kFull, q, 0);
-    if (q >= G) break;
+    if (q >= NQ) break;
     const int g = E.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
     const Walked w = traverse_group<VAR>(T, g, lane, lt, cur, nxt, cl, pl);
@@ -1063,7 +1067,8 @@ void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blo
 
 int walk_block_warps() { return kWarps; }
 
-cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s) {
+cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s,
+                        const uint8_t *g_active) {
   TravArgs t;
   t.part_hi = c.part_hi;
   t.part_lo = c.part_lo;
@@ -1109,7 +1114,7 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   a.perm = c.idx[0];
   const int var = c.p.walk_variant;
   const bool guard = !(a.eps2 > 0.f);
-  const bool fused = walk_is_fused(c.p);
+  const bool fused = walk_is_fused(c.p) || g_active;  // a walk of some groups only is always fused
   cudaError_t e = cudaSuccess;
   auto mark = [&](int end) {
     if (!c.profiling) return;
@@ -1119,11 +1124,12 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   };
   if (fused) {
     // groups by size (largest first), then one kernel walks and evaluates
-    k_size_hist<<<c.num_sms * 4, 256, 0, s>>>(c.d_counts, c.g_beg, c.work_hist);
+    k_size_hist<<<c.num_sms * 4, 256, 0, s>>>(c.d_counts, c.g_beg, g_active, c.work_hist);
     e = cudaGetLastError();
     c.launches++;
     if (e) return e;
-    k_order<true><<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.g_beg, c.work_hist, c.g_order);
+    k_order<true><<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.g_beg, g_active, c.work_hist,
+                                                         c.g_order);
     e = cudaGetLastError();
     c.launches++;
     if (e) return e;
@@ -1149,7 +1155,8 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   e = cudaGetLastError();
   c.launches++;
   if (e) return e;
-  k_order<false><<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.g_beg, c.work_hist, c.g_order);
+  k_order<false><<<c.num_sms * 4, kCostBuckets, 0, s>>>(c.d_counts, c.g_list, c.g_beg, nullptr, c.work_hist,
+                                                        c.g_order);
   e = cudaGetLastError();
   c.launches++;
   if (e) return e;
