@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--mac", type=int, default=0, choices=[0, 1],
                     help="opening criterion: 0 Eq. 1 (default), 1 minimal distance")
     ap.add_argument("--block", action="store_true", help="add the block time-step measurement")
+    ap.add_argument("--block-eta", type=float, default=0.05, help="time-step accuracy parameter eta")
     ap.add_argument("--split", action="store_true",
                     help="split walk (lists through a pool, then a separate evaluation kernel)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
@@ -214,7 +215,7 @@ def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
                       f"theta={theta}, eps={eps}"}
 
 
-def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.02):
+def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.05):
     """Block time-steps on the same workload: one synchronised interval of
     dt_max (rebuild at its start, moment refresh inside it), against stepping
     every body with the smallest step any body used in it (what a shared step
@@ -233,13 +234,12 @@ def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, 
         start = time.perf_counter()
         steps = updates = rebuilds = 0
         deepest = 0
-        while True:
-            tick = tc.block_info()["tick"]
-            if tick >= t0 + sync:
-                break
+        tick = t0
+        while tick < t0 + sync:
             rebuild = tick % sync == 0
             tc.block_step(theta, eps, rebuild=rebuild)
-            info = tc.block_info()
+            info = tc.block_info()  # (the one host synchronisation of a block step)
+            tick = info["tick"]
             steps += 1
             updates += info["active"]
             rebuilds += int(rebuild)
@@ -508,8 +508,8 @@ def main():
     if not args.no_ensemble and args.workload == "plummer":
         ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=3, warmup=2)
     blk = None
-    if args.block and args.workload == "plummer":
-        blk = block_compare(bh, dev, P, V, M, args.theta, EPS, kw)
+    if args.block:
+        blk = block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pos, m, args.theta, eps)
