@@ -102,6 +102,7 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.offs = k.take<int32_t>(S + 1);
   c.minmax = k.take<unsigned long long>(6 * S);
   c.frame = k.take<bh::Frame>(S);
+  c.framef = k.take<bh::FrameF>(S);
   c.sys_root = k.take<int32_t>(S);
   c.frame_ticket = k.take<uint32_t>(1);
   for (int b = 0; b < 2; ++b) {

@@ -21,6 +21,12 @@ struct __align__(32) Frame {
   double x, y, z, w;
 };
 
+// The same frame as floats: the origin as two-float pairs (hi + lo = origin to
+// ~2^-48) and the side L (a power of two, exact), for FP32-only cell geometry.
+struct __align__(32) FrameF {
+  float ohi[3], olo[3], L, pad;
+};
+
 // ------------------------------------------------------------ context
 struct Ctx {
   bh_params p;
@@ -58,6 +64,7 @@ struct Ctx {
   int32_t *offs;                 // [S+1]
   unsigned long long *minmax;    // [S][6] order-preserving bits of min xyz, max xyz
   Frame *frame;                  // [S] origin xyz, L
+  FrameF *framef;                // [S] the same as float pairs
   int32_t *sys_root;             // [S]
   uint32_t *frame_ticket;        // [1]
   // per body

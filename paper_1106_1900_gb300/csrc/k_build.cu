@@ -56,7 +56,7 @@ template <bool FOREST>
 __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos, const double *__restrict__ mass,
                                                  int n, const int32_t *__restrict__ offs, int S,
                                                  unsigned long long *minmax, uint32_t *ticket, Frame *frame,
-                                                 int32_t *status) {
+                                                 FrameF *framef, int32_t *status) {
   __shared__ unsigned long long s_v[kBlock / 32][6];
   __shared__ int s_sys[kBlock / 32];
   __shared__ bool s_last;
@@ -163,6 +163,13 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
       f = Frame{lo[0], lo[1], lo[2], L};
     }
     frame[s] = f;
+    FrameF ff;
+    split2(f.x, ff.ohi[0], ff.olo[0]);
+    split2(f.y, ff.ohi[1], ff.olo[1]);
+    split2(f.z, ff.ohi[2], ff.olo[2]);
+    ff.L = (float)f.w;
+    ff.pad = 0.f;
+    framef[s] = ff;
   }
   if (threadIdx.x == 0) *ticket = 0;
 }
@@ -748,10 +755,11 @@ cudaError_t launch_frame_keys(Ctx &c, const double *pos, const double *mass, cud
   const bool forest = c.n_sys > 1;
   int nb = cdiv(n, 4 * kBlock);
   if (forest)
-    k_bbox<true><<<nb, kBlock, 0, s>>>(pos, mass, n, c.offs, c.n_sys, c.minmax, c.frame_ticket, c.frame, c.d_status);
+    k_bbox<true><<<nb, kBlock, 0, s>>>(pos, mass, n, c.offs, c.n_sys, c.minmax, c.frame_ticket, c.frame, c.framef,
+                                       c.d_status);
   else
     k_bbox<false><<<nb, kBlock, 0, s>>>(pos, mass, n, c.offs, c.n_sys, c.minmax, c.frame_ticket, c.frame,
-                                        c.d_status);
+                                        c.framef, c.d_status);
   if (forest)
     k_keys<true><<<cdiv(n, kBlock), kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, c.key[0], c.idx[0]);
   else

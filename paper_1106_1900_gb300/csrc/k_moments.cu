@@ -28,35 +28,72 @@ namespace {
 constexpr int kBlock = 256;
 
 struct Centre {
-  double c[3];
-  float hi[3], lo[3];
-  float l;
+  float hi[3], lo[3];  // geometric centre as a two-float sum (hi + lo to ~2^-48)
+  float l;             // side
 };
 
-// Geometric centre origin + (i + 1/2) l of the level-k cell holding sorted body i.
+// a + b = s + e exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) -> the same sum with hi the rounded value and |lo| <= ulp(hi)/2
+// (TwoSum: exact whatever the magnitudes).  The walk reads the high part alone
+// (the opening test), so it must be the correctly rounded value.
+__device__ __forceinline__ void renormalise(float &hi, float &lo) {
+  float s, e;
+  two_sum(hi, lo, s, e);
+  hi = s;
+  lo = e;
+}
+
+// Geometric centre origin + (i + 1/2) l of the level-k cell holding sorted
+// body i, l = L 2^-k.  In FP32 when the frame allows: (i + 1/2) l is exact
+// (i < 2^20, l a power of two) and TwoSum adds it to the origin's float pair;
+// otherwise (a side below 2^-100 or above 2^100) in FP64.
 template <bool FOREST>
 __device__ __forceinline__ Centre cell_centre(int k, int i, const uint64_t *__restrict__ skey,
                                               const int32_t *__restrict__ offs, int S,
-                                              const Frame *__restrict__ frame) {
-  int s = FOREST ? sys_of(offs, S, i) : 0;
-  Frame f = frame[s];
-  double l = ldexp(f.w, -k);
-  uint64_t key = skey[i];
-  double o[3] = {f.x, f.y, f.z};
+                                              const Frame *__restrict__ frame, const FrameF *__restrict__ framef) {
+  const int s = FOREST ? sys_of(offs, S, i) : 0;
+  const FrameF f = framef[s];
+  const uint64_t key = skey[i];
   Centre C;
-  for (int a = 0; a < 3; ++a) {
-    uint32_t corner = (k == 0) ? 0u : (compact3(key >> a) >> (kLevels - k));
-    C.c[a] = __dadd_rn(o[a], __dmul_rn((double)corner + 0.5, l));
-    split2(C.c[a], C.hi[a], C.lo[a]);
+  if (f.L > 0x1p-100f && f.L < 0x1p100f) {
+    const float l = ldexpf(f.L, -k);
+    for (int a = 0; a < 3; ++a) {
+      const uint32_t corner = (k == 0) ? 0u : (compact3(key >> a) >> (kLevels - k));
+      float e;
+      two_sum(f.ohi[a], ((float)corner + 0.5f) * l, C.hi[a], e);
+      C.lo[a] = e + f.olo[a];
+      renormalise(C.hi[a], C.lo[a]);  // the sum may have cancelled: lo is not small then
+    }
+    C.l = l;
+  } else {
+    const Frame g = frame[s];
+    const double l = ldexp(g.w, -k);
+    const double o[3] = {g.x, g.y, g.z};
+    for (int a = 0; a < 3; ++a) {
+      const uint32_t corner = (k == 0) ? 0u : (compact3(key >> a) >> (kLevels - k));
+      split2(__dadd_rn(o[a], __dmul_rn((double)corner + 0.5, l)), C.hi[a], C.lo[a]);
+    }
+    C.l = (float)l;
   }
-  C.l = (float)l;
   return C;
 }
 
+// centre of mass = centre + cm (float offsets), as a two-float sum
 __device__ __forceinline__ void write_cell(float4 *mom, int c, const Centre &C, float M, const float cm[3],
                                            const float Q[6], float l) {
   float hi[3], lo[3];
-  for (int a = 0; a < 3; ++a) split2(__dadd_rn(C.c[a], (double)cm[a]), hi[a], lo[a]);
+  for (int a = 0; a < 3; ++a) {
+    float e;
+    two_sum(C.hi[a], cm[a], hi[a], e);
+    lo[a] = e + C.lo[a];
+    renormalise(hi[a], lo[a]);
+  }
   float delta = sqrtf(cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2]);
   mom[4 * (size_t)c + 0] = make_float4(hi[0], hi[1], hi[2], M);
   mom[4 * (size_t)c + 1] = make_float4(lo[0], lo[1], lo[2], delta);
@@ -82,6 +119,7 @@ template <bool FOREST, bool REFRESH>
 __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__ skey,
                                                     const int32_t *__restrict__ offs, int S,
                                                     const Frame *__restrict__ frame,
+                                                    const FrameF *__restrict__ framef,
                                                     const int32_t *__restrict__ counts,
                                                     const int32_t *__restrict__ c_level,
                                                     const int32_t *__restrict__ c_pbeg,
@@ -98,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
     // ---- leaf: from its bodies
     {
       const int k = lv & 31, b = c_pbeg[c], e = c_pend[c];
-      Centre G = cell_centre<FOREST>(k, b, skey, offs, S, frame);
+      Centre G = cell_centre<FOREST>(k, b, skey, offs, S, frame, framef);
       float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, ext = 0.f;
       for (int i = b; i < e; ++i) {
         float4 h = part_hi[i], l = part_lo[i];
@@ -138,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
       if (atomicAdd(&c_ctr[p], 1u) != nch - 1) break;
       __threadfence();
       const int k = c_level[p] & 31;
-      Centre G = cell_centre<FOREST>(k, c_pbeg[p], skey, offs, S, frame);
+      Centre G = cell_centre<FOREST>(k, c_pbeg[p], skey, offs, S, frame, framef);
       const int f = c_first[p];
       float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, lch = 0.f;
       for (uint32_t j = 0; j < nch; ++j) {
@@ -219,6 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ 
                                                     const uint64_t *__restrict__ skey,
                                                     const int32_t *__restrict__ offs, int S,
                                                     const Frame *__restrict__ frame,
+                                                    const FrameF *__restrict__ framef,
                                                     const int32_t *__restrict__ c_level,
                                                     const int32_t *__restrict__ c_pbeg, float4 *mac, uint32_t *queue,
                                                     unsigned long long *pool_ctr, uint32_t *work_hist) {
@@ -232,7 +271,7 @@ __global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ 
     for (int i = threadIdx.x; i < 2 * kCostBuckets; i += blockDim.x) work_hist[i] = 0;
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-    const Centre G = cell_centre<FOREST>(c_level[c] & 31, c_pbeg[c], skey, offs, S, frame);
+    const Centre G = cell_centre<FOREST>(c_level[c] & 31, c_pbeg[c], skey, offs, S, frame, framef);
     mac[c] = make_float4(G.hi[0], G.hi[1], G.hi[2], 0.5f * G.l);
   }
 }
@@ -243,11 +282,11 @@ template <bool REFRESH>
 static void moments_launch(Ctx &c, cudaStream_t s) {
   const int nb = c.num_sms * 8;
   if (c.n_sys > 1)
-    k_moments<true, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level,
+    k_moments<true, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.d_counts, c.c_level,
                                                    c.c_pbeg, c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr,
                                                    c.part_hi, c.part_lo, c.c_mom);
   else
-    k_moments<false, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.d_counts, c.c_level,
+    k_moments<false, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.d_counts, c.c_level,
                                                     c.c_pbeg, c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr,
                                                     c.part_hi, c.part_lo, c.c_mom);
 }
@@ -272,10 +311,10 @@ cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s) {
   float inv = (theta > 0.f) ? 1.0f / theta : INFINITY;
   if (c.p.mac == 1) {
     if (c.n_sys > 1)
-      k_mac_box<true><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.c_level,
+      k_mac_box<true><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.c_level,
                                                        c.c_pbeg, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
     else
-      k_mac_box<false><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.c_level,
+      k_mac_box<false><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.c_level,
                                                         c.c_pbeg, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
   } else {
     k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr,
