@@ -150,6 +150,8 @@ def main(argv=None):
     ap.add_argument("--theta", type=float, default=0.5)
     ap.add_argument("--eps", type=float, default=0.005)
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy"],
+                    help="galaxy: Hernquist sphere + exponential disk, 8,388,608 bodies (--n ignored)")
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--out", default=TUNED)
     args = ap.parse_args(argv)
@@ -158,13 +160,16 @@ def main(argv=None):
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import ics
 
-    pos, vel, m = ics.plummer(args.n, args.seed)
+    if args.workload == "galaxy":
+        pos, vel, m = ics.galaxy(4194304, 4194304, 3)
+    else:
+        pos, vel, m = ics.plummer(args.n, args.seed)
     dev = torch.device("cuda", 0)
     P, V, M = (torch.from_numpy(a).to(dev) for a in (pos, vel, m))
     best, trials = autotune(P, V, M, args.theta, args.eps, steps=args.steps,
                             log=lambda r: print(json.dumps(r), flush=True))
     table = load_table(args.out)
-    table[key_for(args.n, args.theta)] = {**best, "eps": args.eps, "trials": trials}
+    table[key_for(len(pos), args.theta, args.workload)] = {**best, "eps": args.eps, "trials": trials}
     with open(args.out, "w") as f:
         json.dump(table, f, indent=1, sort_keys=True)
     print(json.dumps({"best": best}))
