@@ -22,6 +22,9 @@ and a galaxy merger whose initial conditions are not public, §4.2.2):
 * :func:`ensemble` -- many independent Plummer clusters of log-uniform
   sizes and uniform scale radii, returned back to back with their
   system offsets.
+* :func:`nested` -- a Plummer sphere holding a second, far more compact
+  Plummer cluster: more bodies share one cell of the 20th level than any
+  leaf may hold, the case deeper keys are for (App. B).
 """
 from __future__ import annotations
 
@@ -29,7 +32,7 @@ import math
 
 import numpy as np
 
-__all__ = ["plummer", "galaxy", "ensemble", "subsample"]
+__all__ = ["plummer", "galaxy", "ensemble", "nested", "subsample"]
 
 _VIRIAL_R = 3.0 * math.pi / 16.0  # Plummer scale length in virial units
 
@@ -149,6 +152,21 @@ def ensemble(n_sys: int = 512, seed: int = 5, n_min: int = 1024, n_max: int = 65
     offsets = np.zeros(n_sys + 1, dtype=np.int64)
     offsets[1:] = np.cumsum(sizes)
     return np.ascontiguousarray(pos), np.ascontiguousarray(vel), mass, offsets
+
+
+def nested(n: int, seed: int, n_core: int, core_scale: float = 1e-6, at=(0.3, 0.1, -0.2)):
+    """A Plummer sphere of ``n - n_core`` bodies and, centred at ``at``, a
+    Plummer cluster of ``n_core`` bodies shrunk by ``core_scale`` (its
+    velocities scaled to stay bound: by ``sqrt(f / core_scale)``, f its mass
+    fraction).  Equal masses 1/n; the two parts use seeds ``seed`` and
+    ``seed + 1``.  Returns ``(pos, vel, mass)``."""
+    pa, va, _ = plummer(n - n_core, seed)
+    pb, vb, _ = plummer(n_core, seed + 1)
+    f = n_core / n
+    pos = np.concatenate([pa, pb * core_scale + np.asarray(at, dtype=np.float64)])
+    vel = np.concatenate([va, vb * math.sqrt(f / core_scale)])
+    mass = np.full(n, 1.0 / n)
+    return np.ascontiguousarray(pos), np.ascontiguousarray(vel), mass
 
 
 def subsample(n: int, k: int, seed: int) -> np.ndarray:

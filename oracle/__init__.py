@@ -30,7 +30,8 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-LEVELS = 20
+LEVELS = 20  # the paper's 60-bit keys
+LEVELS_MAX = 30  # 90-bit keys (App. B: the way past 20 levels)
 
 
 def build(force: bool = False) -> str:
@@ -56,12 +57,12 @@ def _load():
             sig = {
                 "or_dilate10": (u32, [u32]),
                 "or_frames": (ctypes.c_int, [i64, p, i32, p, p]),
-                "or_keys": (ctypes.c_int, [i64, p, i32, p, p, p, p, p]),
-                "or_sort": (ctypes.c_int, [i64, p, p, p]),
-                "or_build_levels": (i64, [i64, p, p, i32, i64, p, p, p, p, p]),
-                "or_link": (ctypes.c_int, [i64, p, p, p, p, p, p, p]),
+                "or_keys": (ctypes.c_int, [i64, p, i32, p, p, i32, p, p, p, p]),
+                "or_sort": (ctypes.c_int, [i64, p, p, i32, p, p]),
+                "or_build_levels": (i64, [i64, p, p, i32, p, i32, i64, p, p, p, p, p]),
+                "or_link": (ctypes.c_int, [i64, p, p, p, p, p, i32, p, p, p]),
                 "or_groups": (i64, [i64, p, p, p, p, p, p, i32, i64, p, p]),
-                "or_moments": (ctypes.c_int, [i64, p, p, p, p, p, p, p, p, p, p, p, p, p, p]),
+                "or_moments": (ctypes.c_int, [i64, p, p, p, p, p, p, p, p, i32, p, p, p, p, p, p]),
                 "or_walk": (ctypes.c_int, [i64, p, p, p, p, p, i64, p, p, p, p, p, p, p, p, p, p, p, i64, p,
                                            p, dbl, dbl, i32, p, p, p, p]),
                 "or_direct": (ctypes.c_int, [i64, p, p, i32, p, i64, p, dbl, p, p]),
@@ -105,40 +106,63 @@ def frames(pos: np.ndarray, offsets=None) -> np.ndarray:
     return fr
 
 
-def keys(pos: np.ndarray, offsets=None, frame=None):
-    """Quantised coordinates ``q[N,3]``, 60-bit Morton keys and system ids."""
+def _check_levels(levels: int) -> int:
+    levels = int(levels)
+    if not LEVELS <= levels <= LEVELS_MAX:
+        raise ValueError(f"key depth {levels} outside {LEVELS}..{LEVELS_MAX}")
+    return levels
+
+
+def keys_split(pos: np.ndarray, offsets=None, frame=None, levels: int = LEVELS):
+    """Quantised coordinates ``q[N,3]`` (2^levels cells per axis), the
+    3*levels-bit Morton keys as two words -- ``key_hi`` (levels 1..20, the
+    top 60 bits) and ``key_lo`` (levels 21..``levels``, the low bits; 0 for
+    20-level keys) -- and system ids (App. B)."""
+    levels = _check_levels(levels)
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     off = _offsets(len(pos), offsets)
     fr = frames(pos, off) if frame is None else np.ascontiguousarray(frame, dtype=np.float64)
     n = len(pos)
     q = np.zeros((n, 3), dtype=np.int32)
-    key = np.zeros(n, dtype=np.uint64)
+    key_hi = np.zeros(n, dtype=np.uint64)
+    key_lo = np.zeros(n, dtype=np.uint64)
     sys_ = np.zeros(n, dtype=np.int32)
-    _load().or_keys(n, _p(pos), len(off) - 1, _p(off), _p(fr), _p(q), _p(key), _p(sys_))
+    _load().or_keys(n, _p(pos), len(off) - 1, _p(off), _p(fr), levels, _p(q), _p(key_hi), _p(key_lo), _p(sys_))
+    return q, key_hi, key_lo, sys_
+
+
+def keys(pos: np.ndarray, offsets=None, frame=None):
+    """Quantised coordinates ``q[N,3]``, 60-bit Morton keys and system ids."""
+    q, key, _, sys_ = keys_split(pos, offsets, frame, LEVELS)
     return q, key, sys_
 
 
-def sort_perm(key: np.ndarray, sys_: np.ndarray) -> np.ndarray:
-    """Stable order by (system, key): ``perm[i]`` = input index of the i-th body (§2.1)."""
+def sort_perm(key: np.ndarray, sys_: np.ndarray, key_lo=None, levels: int = LEVELS) -> np.ndarray:
+    """Stable order by (system, key): ``perm[i]`` = input index of the i-th body (§2.1).
+    Deeper keys pass their low word as ``key_lo``."""
+    levels = _check_levels(levels)
     key = np.ascontiguousarray(key, dtype=np.uint64)
+    lo = np.zeros_like(key) if key_lo is None else np.ascontiguousarray(key_lo, dtype=np.uint64)
     sys_ = np.ascontiguousarray(sys_, dtype=np.int32)
     perm = np.zeros(len(key), dtype=np.int64)
-    _load().or_sort(len(key), _p(key), _p(sys_), _p(perm))
+    _load().or_sort(len(key), _p(key), _p(lo), levels, _p(sys_), _p(perm))
     return perm
 
 
-def cell_bound(n: int, n_leaf: int, n_sys: int = 1) -> int:
+def cell_bound(n: int, n_leaf: int, n_sys: int = 1, levels: int = LEVELS) -> int:
     """Upper bound on the cell count: at most n/(N_leaf+1) nodes per level
-    (levels 0..19) and at most one leaf per body."""
-    return 20 * (n // (n_leaf + 1)) + n + n_sys + 1
+    (levels 0..levels-1) and at most one leaf per body."""
+    return levels * (n // (n_leaf + 1)) + n + n_sys + 1
 
 
 class Tree:
     """The oracle's tree: every array is in sorted (system, key) order."""
 
 
-def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None) -> Tree:
-    """§2.1 + §2.2 + §3.2: keys, sort, level-by-level cells, link, groups, moments."""
+def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None, levels: int = LEVELS) -> Tree:
+    """§2.1 + §2.2 + §3.2: keys, sort, level-by-level cells, link, groups,
+    moments; ``levels`` is the key depth (20, or up to 30 with 90-bit keys)."""
+    levels = _check_levels(levels)
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     mass = np.ascontiguousarray(mass, dtype=np.float64)
@@ -146,23 +170,24 @@ def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None) -> T
     off = _offsets(n, offsets)
     nsys = len(off) - 1
     t = Tree()
-    t.n, t.n_leaf, t.n_crit, t.offsets = n, n_leaf, n_crit, off
+    t.n, t.n_leaf, t.n_crit, t.offsets, t.levels = n, n_leaf, n_crit, off, levels
     t.frame = frames(pos, off)
-    t.q, t.key, t.sys = keys(pos, off, t.frame)
-    t.perm = sort_perm(t.key, t.sys)
+    t.q, t.key, t.key_lo, t.sys = keys_split(pos, off, t.frame, levels)
+    t.perm = sort_perm(t.key, t.sys, t.key_lo, levels)
     t.skey = np.ascontiguousarray(t.key[t.perm])
+    t.skey_lo = np.ascontiguousarray(t.key_lo[t.perm])
     t.ssys = np.ascontiguousarray(t.sys[t.perm])
     t.spos = np.ascontiguousarray(pos[t.perm])
     t.smass = np.ascontiguousarray(mass[t.perm])
     t.sq = np.ascontiguousarray(t.q[t.perm])
-    cap = cell_bound(n, n_leaf, nsys)
+    cap = cell_bound(n, n_leaf, nsys, levels)
     level = np.zeros(cap, dtype=np.int32)
     pbeg = np.zeros(cap, dtype=np.int64)
     pend = np.zeros(cap, dtype=np.int64)
     is_leaf = np.zeros(cap, dtype=np.int32)
     csys = np.zeros(cap, dtype=np.int32)
-    C = lib.or_build_levels(n, _p(t.skey), _p(t.ssys), n_leaf, cap, _p(level), _p(pbeg), _p(pend), _p(is_leaf),
-                            _p(csys))
+    C = lib.or_build_levels(n, _p(t.skey), _p(t.skey_lo), levels, _p(t.ssys), n_leaf, cap, _p(level), _p(pbeg),
+                            _p(pend), _p(is_leaf), _p(csys))
     if C < 0:
         raise RuntimeError("oracle: cell capacity exceeded")
     t.C = int(C)
@@ -171,8 +196,8 @@ def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None) -> T
     t.parent = np.zeros(C, dtype=np.int64)
     t.first_child = np.zeros(C, dtype=np.int64)
     t.n_children = np.zeros(C, dtype=np.int32)
-    rc = lib.or_link(C, _p(t.level), _p(t.pbeg), _p(t.csys), _p(t.skey), _p(t.parent), _p(t.first_child),
-                     _p(t.n_children))
+    rc = lib.or_link(C, _p(t.level), _p(t.pbeg), _p(t.csys), _p(t.skey), _p(t.skey_lo), levels, _p(t.parent),
+                     _p(t.first_child), _p(t.n_children))
     if rc != 0:
         raise RuntimeError("oracle: link failed")
     gb = np.zeros(n + 1, dtype=np.int64)
@@ -194,7 +219,7 @@ def build_tree(pos, mass, n_leaf: int = 16, n_crit: int = 64, offsets=None) -> T
     t.size = np.zeros(C)
     t.delta = np.zeros(C)
     lib.or_moments(C, _p(t.level), _p(t.pbeg), _p(t.pend), _p(t.csys), _p(t.spos), _p(t.smass), _p(t.sq),
-                   _p(t.frame), _p(t.M), _p(t.com), _p(t.Q), _p(t.ctr), _p(t.size), _p(t.delta))
+                   _p(t.frame), levels, _p(t.M), _p(t.com), _p(t.Q), _p(t.ctr), _p(t.size), _p(t.delta))
     return t
 
 
@@ -230,9 +255,10 @@ def walk(t: Tree, theta: float, eps: float, groups=None, mac: int = 0):
     return acc, pot, stats
 
 
-def tree_forces(pos, mass, theta: float, eps: float, n_leaf: int = 16, n_crit: int = 64, offsets=None, mac: int = 0):
+def tree_forces(pos, mass, theta: float, eps: float, n_leaf: int = 16, n_crit: int = 64, offsets=None, mac: int = 0,
+                levels: int = LEVELS):
     """Build + walk all groups; accelerations and potentials in INPUT order."""
-    t = build_tree(pos, mass, n_leaf, n_crit, offsets)
+    t = build_tree(pos, mass, n_leaf, n_crit, offsets, levels)
     acc_s, pot_s, stats = walk(t, theta, eps, mac=mac)
     acc = np.empty_like(acc_s)
     pot = np.empty_like(pot_s)
@@ -337,7 +363,7 @@ def refresh_tree(t: Tree, spos_new) -> Tree:
     r.M, r.com, r.Q = np.zeros(C), np.zeros((C, 3)), np.zeros((C, 6))
     r.ctr, r.size, r.delta = np.zeros((C, 3)), np.zeros(C), np.zeros(C)
     lib.or_moments(C, _p(t.level), _p(t.pbeg), _p(t.pend), _p(t.csys), _p(r.spos), _p(t.smass), _p(t.sq),
-                   _p(t.frame), _p(r.M), _p(r.com), _p(r.Q), _p(r.ctr), _p(r.size), _p(r.delta))
+                   _p(t.frame), t.levels, _p(r.M), _p(r.com), _p(r.Q), _p(r.ctr), _p(r.size), _p(r.delta))
     lib.or_refresh_sizes(C, _p(t.is_leaf), _p(t.pbeg), _p(t.pend), _p(t.first_child), _p(t.n_children),
                          _p(r.spos), _p(r.ctr), _p(r.size))
     return r

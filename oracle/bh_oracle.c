@@ -23,12 +23,16 @@
  * Where the paper is silent the readings are:
  *   - frame: origin = per-axis minimum; L = smallest power of two not
  *     below E*(1+2^-20), E the largest per-axis extent; L = 1 if E = 0.
- *   - quantisation: q = floor((x - origin) * 2^20/L), clamped to [0, 2^20-1].
- *   - key: bit b of qx, qy, qz at bits 3b, 3b+1, 3b+2 (60 bits, 20 levels);
- *     a forest orders by (system, key).
+ *   - quantisation: q = floor((x - origin) * 2^D/L), clamped to [0, 2^D-1],
+ *     D the key depth in levels: 20 (the paper's 60-bit keys) or up to 30
+ *     (the 90-bit keys App. B names as the way past 20 levels).
+ *   - key: bit b of qx, qy, qz at bits 3b, 3b+1, 3b+2 (3D bits, D levels),
+ *     stored as two words: hi = levels 1..20 (the top 60 bits), lo = levels
+ *     21..D (the low 3(D-20) bits, 0 when D = 20); a forest orders by
+ *     (system, key).
  *   - sort ties keep input order.
  *   - level 0 is the root; a cell with n <= N_leaf, or any cell at level
- *     20, is a leaf.
+ *     D, is a leaf.
  *   - a group is a cell with n <= N_crit whose parent has n > N_crit (or a
  *     root with n <= N_crit); a leaf with n > N_crit is cut into
  *     consecutive chunks of N_crit bodies.
@@ -49,8 +53,17 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_LEVELS 20
-#define OR_QMAX 1048576 /* 2^20 cells per axis at the deepest level */
+#define OR_LEVELS_MAX 30 /* deepest key: 90 bits */
+
+typedef unsigned __int128 or_key_t; /* a whole 3D-bit key */
+
+static int bad_levels(int D) { return D < 20 || D > OR_LEVELS_MAX; }
+
+/* The whole key of body i from its two stored words. */
+static or_key_t full_key(const uint64_t *hi, const uint64_t *lo, int D, int64_t i)
+{
+    return ((or_key_t)hi[i] << (3 * (D - 20))) | (or_key_t)lo[i];
+}
 
 /* ------------------------------------------------------------------ App. B */
 
@@ -99,28 +112,33 @@ int or_frames(int64_t n, const double *pos, int32_t nsys, const int64_t *offs, d
     return 0;
 }
 
-/* Quantise every body in its system's frame and form its 60-bit Morton key
- * by interleaving bit b of (qx, qy, qz) into bits (3b, 3b+1, 3b+2). */
-int or_keys(int64_t n, const double *pos, int32_t nsys, const int64_t *offs, const double *frame,
-            int32_t *q, uint64_t *key, int32_t *sys)
+/* Quantise every body in its system's frame (2^D cells per axis) and form
+ * its 3D-bit Morton key by interleaving bit b of (qx, qy, qz) into bits
+ * (3b, 3b+1, 3b+2); stored as key_hi (levels 1..20) and key_lo (21..D). */
+int or_keys(int64_t n, const double *pos, int32_t nsys, const int64_t *offs, const double *frame, int32_t D,
+            int32_t *q, uint64_t *key_hi, uint64_t *key_lo, int32_t *sys)
 {
     (void)n;
+    if (bad_levels(D)) return -1;
+    const double qmax = ldexp(1.0, D);
+    const int lo_bits = 3 * (D - 20);
     for (int32_t s = 0; s < nsys; ++s) {
-        double scale = (double)OR_QMAX / frame[4 * s + 3];
+        double scale = qmax / frame[4 * s + 3];
         for (int64_t i = offs[s]; i < offs[s + 1]; ++i) {
             int64_t qi[3];
             for (int a = 0; a < 3; ++a) {
                 double t = floor((pos[3 * i + a] - frame[4 * s + a]) * scale);
                 if (t < 0.0) t = 0.0;
-                if (t > (double)(OR_QMAX - 1)) t = (double)(OR_QMAX - 1);
+                if (t > qmax - 1.0) t = qmax - 1.0;
                 qi[a] = (int64_t)t;
                 q[3 * i + a] = (int32_t)qi[a];
             }
-            uint64_t k = 0;
-            for (int b = 0; b < OR_LEVELS; ++b)
+            or_key_t k = 0;
+            for (int b = 0; b < D; ++b)
                 for (int a = 0; a < 3; ++a)
-                    k |= (uint64_t)((qi[a] >> b) & 1) << (3 * b + a);
-            key[i] = k;
+                    k |= (or_key_t)((qi[a] >> b) & 1) << (3 * b + a);
+            key_hi[i] = (uint64_t)(k >> lo_bits);
+            key_lo[i] = (uint64_t)(k & (((or_key_t)1 << lo_bits) - 1));
             sys[i] = s;
         }
     }
@@ -129,22 +147,27 @@ int or_keys(int64_t n, const double *pos, int32_t nsys, const int64_t *offs, con
 
 /* ------------------------------------------------------------ §2.1 sort */
 
-static const uint64_t *g_key;
+static const uint64_t *g_key_hi, *g_key_lo;
 static const int32_t *g_sys;
+static int g_levels;
 
 static int cmp_sys_key_index(const void *pa, const void *pb)
 {
     int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;
     if (g_sys[a] != g_sys[b]) return g_sys[a] < g_sys[b] ? -1 : 1;
-    if (g_key[a] != g_key[b]) return g_key[a] < g_key[b] ? -1 : 1;
+    or_key_t ka = full_key(g_key_hi, g_key_lo, g_levels, a), kb = full_key(g_key_hi, g_key_lo, g_levels, b);
+    if (ka != kb) return ka < kb ? -1 : 1;
     return (a < b) ? -1 : (a > b); /* stable: equal keys keep input order */
 }
 
 /* perm[i] = input index of the i-th body in (system, key) order. */
-int or_sort(int64_t n, const uint64_t *key, const int32_t *sys, int64_t *perm)
+int or_sort(int64_t n, const uint64_t *key_hi, const uint64_t *key_lo, int32_t D, const int32_t *sys, int64_t *perm)
 {
+    if (bad_levels(D)) return -1;
     for (int64_t i = 0; i < n; ++i) perm[i] = i;
-    g_key = key;
+    g_key_hi = key_hi;
+    g_key_lo = key_lo;
+    g_levels = D;
     g_sys = sys;
     qsort(perm, (size_t)n, sizeof(int64_t), cmp_sys_key_index);
     return 0;
@@ -152,36 +175,38 @@ int or_sort(int64_t n, const uint64_t *key, const int32_t *sys, int64_t *perm)
 
 /* ------------------------------------------- §2.1, Fig. 1: level by level */
 
-/* Mask keeping the top 3k bits of a 60-bit key (footnote to §2.1). */
-static uint64_t level_mask(int k)
+/* Mask keeping the top 3k bits of a 3D-bit key (footnote to §2.1). */
+static or_key_t level_mask(int k, int D)
 {
     if (k == 0) return 0;
-    uint64_t all = (1ull << 60) - 1;
-    return all & ~((1ull << (60 - 3 * k)) - 1);
+    or_key_t all = ((or_key_t)1 << (3 * D)) - 1;
+    return all & ~(((or_key_t)1 << (3 * (D - k))) - 1);
 }
 
-/* skey/ssys: keys and systems in sorted order.  For every level, the keys of
- * the bodies not yet in a leaf are masked; consecutive bodies with equal
- * masked keys (and the same system) form one cell; cells with at most N_leaf
- * bodies (or at level 20) become leaves and flag their bodies.  The loop
- * stops when every body is in a leaf.  Returns the cell count, or -1 if
- * more than cap cells would be made. */
-int64_t or_build_levels(int64_t n, const uint64_t *skey, const int32_t *ssys, int32_t n_leaf, int64_t cap,
-                        int32_t *level, int64_t *pbeg, int64_t *pend, int32_t *is_leaf, int32_t *csys)
+/* skey/ssys: keys (two words each) and systems in sorted order.  For every
+ * level, the keys of the bodies not yet in a leaf are masked; consecutive
+ * bodies with equal masked keys (and the same system) form one cell; cells
+ * with at most N_leaf bodies (or at level D) become leaves and flag their
+ * bodies.  The loop stops when every body is in a leaf.  Returns the cell
+ * count, or -1 if more than cap cells would be made. */
+int64_t or_build_levels(int64_t n, const uint64_t *skey_hi, const uint64_t *skey_lo, int32_t D,
+                        const int32_t *ssys, int32_t n_leaf, int64_t cap, int32_t *level, int64_t *pbeg,
+                        int64_t *pend, int32_t *is_leaf, int32_t *csys)
 {
+    if (bad_levels(D)) return -1;
     unsigned char *flag = (unsigned char *)calloc((size_t)(n > 0 ? n : 1), 1);
     int64_t C = 0;
-    for (int k = 0; k <= OR_LEVELS; ++k) {
-        uint64_t mask = level_mask(k);
+    for (int k = 0; k <= D; ++k) {
+        or_key_t mask = level_mask(k, D);
         int64_t made = 0;
         int64_t i = 0;
         while (i < n) {
             if (flag[i]) { ++i; continue; }
-            uint64_t mk = skey[i] & mask;
+            or_key_t mk = full_key(skey_hi, skey_lo, D, i) & mask;
             int64_t j = i + 1;
-            while (j < n && !flag[j] && ssys[j] == ssys[i] && (skey[j] & mask) == mk) ++j;
+            while (j < n && !flag[j] && ssys[j] == ssys[i] && (full_key(skey_hi, skey_lo, D, j) & mask) == mk) ++j;
             if (C >= cap) { free(flag); return -1; }
-            int leaf = (j - i <= n_leaf) || (k == OR_LEVELS);
+            int leaf = (j - i <= n_leaf) || (k == D);
             level[C] = k;
             pbeg[C] = i;
             pend[C] = j;
@@ -202,14 +227,15 @@ int64_t or_build_levels(int64_t n, const uint64_t *skey, const int32_t *ssys, in
 /* §2.1, Fig. 2: every cell finds its parent by a binary search of its masked
  * key among the cells one level up (sorted by system and key), increments
  * the parent's child counter and offers itself as the first child. */
-int or_link(int64_t C, const int32_t *level, const int64_t *pbeg, const int32_t *csys, const uint64_t *skey,
-            int64_t *parent, int64_t *first_child, int32_t *n_children)
+int or_link(int64_t C, const int32_t *level, const int64_t *pbeg, const int32_t *csys, const uint64_t *skey_hi,
+            const uint64_t *skey_lo, int32_t D, int64_t *parent, int64_t *first_child, int32_t *n_children)
 {
+    if (bad_levels(D)) return -1;
     /* start of each level in the cell array */
-    int64_t lstart[OR_LEVELS + 2];
-    for (int k = 0; k <= OR_LEVELS + 1; ++k) lstart[k] = C;
+    int64_t lstart[OR_LEVELS_MAX + 2];
+    for (int k = 0; k <= D + 1; ++k) lstart[k] = C;
     for (int64_t c = C - 1; c >= 0; --c) lstart[level[c]] = c;
-    for (int k = OR_LEVELS; k >= 0; --k)
+    for (int k = D; k >= 0; --k)
         if (lstart[k] > lstart[k + 1]) lstart[k] = lstart[k + 1];
     for (int64_t c = 0; c < C; ++c) {
         parent[c] = -1;
@@ -219,12 +245,12 @@ int or_link(int64_t C, const int32_t *level, const int64_t *pbeg, const int32_t 
     for (int64_t c = 0; c < C; ++c) {
         int k = level[c];
         if (k == 0) continue;
-        uint64_t want = skey[pbeg[c]] & level_mask(k - 1);
+        or_key_t want = full_key(skey_hi, skey_lo, D, pbeg[c]) & level_mask(k - 1, D);
         int32_t s = csys[c];
         int64_t lo = lstart[k - 1], hi = lstart[k] - 1, found = -1;
         while (lo <= hi) {
             int64_t mid = lo + (hi - lo) / 2;
-            uint64_t mk = skey[pbeg[mid]] & level_mask(k - 1);
+            or_key_t mk = full_key(skey_hi, skey_lo, D, pbeg[mid]) & level_mask(k - 1, D);
             int32_t ms = csys[mid];
             if (ms == s && mk == want) { found = mid; break; }
             if (ms < s || (ms == s && mk < want)) lo = mid + 1;
@@ -280,9 +306,10 @@ int64_t or_groups(int64_t C, const int32_t *level, const int64_t *pbeg, const in
  * i the cell's integer corner (top k bits of the body's quantised
  * coordinate); delta = |com - ctr|. */
 int or_moments(int64_t C, const int32_t *level, const int64_t *pbeg, const int64_t *pend, const int32_t *csys,
-               const double *spos, const double *smass, const int32_t *sq, const double *frame,
+               const double *spos, const double *smass, const int32_t *sq, const double *frame, int32_t D,
                double *M, double *com, double *Q, double *ctr, double *size, double *delta)
 {
+    if (bad_levels(D)) return -1;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t c = 0; c < C; ++c) {
         int k = level[c];
@@ -290,7 +317,7 @@ int or_moments(int64_t C, const int32_t *level, const int64_t *pbeg, const int64
         double l = frame[4 * s + 3] / (double)(1u << k);
         double g[3];
         for (int a = 0; a < 3; ++a) {
-            int64_t corner = (int64_t)sq[3 * pbeg[c] + a] >> (OR_LEVELS - k);
+            int64_t corner = (int64_t)sq[3 * pbeg[c] + a] >> (D - k);
             g[a] = frame[4 * s + a] + ((double)corner + 0.5) * l;
         }
         double m = 0.0, cm[3] = {0, 0, 0};

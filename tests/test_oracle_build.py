@@ -126,20 +126,22 @@ def test_sort_matches_numpy_stable():
 def brute_octree(t, n_leaf):
     """Recursive insertion-free octree over the sorted bodies, straight from the
     definition: split a cell into its occupied octants (by the next bit of the
-    quantised coordinates) until it holds <= N_leaf bodies or is at level 20."""
+    quantised coordinates) until it holds <= N_leaf bodies or is at the key
+    depth (level 20 for the paper's 60-bit keys)."""
     q = t.sq
+    depth = getattr(t, "levels", 20)
     cells = []
 
     def rec(b, e, k, parent, s):
         n = e - b
-        leaf = n <= n_leaf or k == 20
+        leaf = n <= n_leaf or k == depth
         me = len(cells)
         cells.append({"level": k, "sys": s, "pbeg": b, "pend": e, "leaf": leaf, "parent": parent, "kids": []})
         if parent >= 0:
             cells[parent]["kids"].append(me)
         if leaf:
             return
-        sh = 19 - k
+        sh = depth - 1 - k
         octant = ((q[b:e, 0] >> sh) & 1) | (((q[b:e, 1] >> sh) & 1) << 1) | (((q[b:e, 2] >> sh) & 1) << 2)
         assert np.all(np.diff(octant) >= 0), "sorted order must list octants in order"
         for o in range(8):
