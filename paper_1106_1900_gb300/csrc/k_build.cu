@@ -453,6 +453,7 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
   __shared__ uint64_t s_key[kBlock + 2 * kHalo];
   __shared__ int8_t s_wl[kBlock + kHalo];  // lcp of windows of N_leaf + 1 keys starting at b0 - kHalo + t
   __shared__ int8_t s_wc[kBlock + kHalo];  // lcp of windows of N_crit + 1 keys
+  __shared__ int8_t s_tl[kBlock + kHalo], s_tc[kBlock + kHalo];  // doubling buffers
   const int b0 = blockIdx.x * kBlock;
   for (int t = threadIdx.x; t < kBlock + 2 * kHalo; t += kBlock) {
     int i = b0 - kHalo + t;
@@ -477,6 +478,30 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
     s_wc[t] = wc;
   }
   __syncthreads();
+  // the largest lcp over the N + 1 windows holding a body is a sliding maximum
+  // of fixed length: one sparse-table level T[x] = max(w[x .. x + 2^j - 1]),
+  // j = floor(log2(N + 1)), built by j doublings, answers it with two reads
+  const int len = kBlock + kHalo;
+  const int jl = 31 - __clz(n_leaf + 1), jc = 31 - __clz(n_crit + 1);
+  int8_t *al = s_wl, *bl = s_tl, *ac = s_wc, *bc = s_tc;
+  for (int m = 0; m < max(jl, jc); ++m) {
+    const int d = 1 << m;
+    for (int t = threadIdx.x; t < len; t += kBlock) {
+      if (m < jl) bl[t] = (int8_t)max((int)al[t], (t + d < len) ? (int)al[t + d] : -1);
+      if (m < jc) bc[t] = (int8_t)max((int)ac[t], (t + d < len) ? (int)ac[t + d] : -1);
+    }
+    __syncthreads();
+    if (m < jl) {
+      int8_t *x = al;
+      al = bl;
+      bl = x;
+    }
+    if (m < jc) {
+      int8_t *x = ac;
+      ac = bc;
+      bc = x;
+    }
+  }
   const int i = b0 + threadIdx.x;
   const bool ok = i < n;
   int lo = 1, hi = 0, gs = 0;
@@ -485,16 +510,10 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
     if (FOREST) sb = offs[sys_of(offs, S, i)];
     const int t = threadIdx.x + kHalo;  // position of i in s_key
     int prev = (i > sb) ? key_lcp(s_key[t - 1], s_key[t]) : -1;
-    // windows of N+1 keys starting at i-N .. i (a window's lcp is -1 where it leaves the system)
-    int wl = -1, wc = -1;
-    for (int q = 0; q <= n_leaf; ++q) {
-      if (i - q < sb) break;
-      wl = max(wl, (int)s_wl[threadIdx.x + kHalo - q]);
-    }
-    for (int q = 0; q <= n_crit; ++q) {
-      if (i - q < sb) break;
-      wc = max(wc, (int)s_wc[threadIdx.x + kHalo - q]);
-    }
+    // windows of N+1 keys starting at i-N .. i (a window's lcp is -1 where it
+    // leaves the system, so windows starting before the system's first body count nothing)
+    const int wl = max((int)al[t - n_leaf], (int)al[t + 1 - (1 << jl)]);
+    const int wc = max((int)ac[t - n_crit], (int)ac[t + 1 - (1 << jc)]);
     int lam = min(wl + 1, kLevels);
     int mu = wc + 1;  // 21: even the level-20 cell holds more than N_crit bodies
     lo = prev + 1;
