@@ -74,7 +74,10 @@ def parse():
     ap.add_argument("--split", action="store_true",
                     help="split walk (lists through a pool, then a separate evaluation kernel)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
-    ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy"],
+    ap.add_argument("--key-levels", type=int, default=20,
+                    help="key depth D (20: the paper's 60-bit keys; up to 30: 90-bit keys)")
+    ap.add_argument("--list-capacity", type=int, default=0, help="longest interaction list (0: library default)")
+    ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy", "nested"],
                     help="plummer: N-body Plummer sphere (--n); galaxy: Hernquist sphere + exponential disk, "
                          "8,388,608 bodies")
     return ap.parse_args()
@@ -403,12 +406,18 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     bh.load()
-    eps = EPS
+    eps, dt = EPS, DT
     if args.workload == "galaxy":
         pos, vel, m = ics.galaxy(4194304, 4194304, 3 + rank)
         eps = 0.01
         workload = (f"galaxy: Hernquist sphere (a=1, M=1) + exponential disk (R_d=1, z0=0.1, M=0.2), "
                     f"N={len(pos)} per GPU (seed 3+rank), theta={args.theta}, eps={eps}, dt=1/64")
+    elif args.workload == "nested":
+        n_core = args.n // 16
+        pos, vel, m = ics.nested(args.n, SEED + rank, n_core)
+        eps, dt = 1e-7, 2.0 ** -32  # a step well below the cluster's crossing time (~1e-8)
+        workload = (f"nested: Plummer N={args.n} per GPU holding a Plummer cluster of {n_core} bodies shrunk "
+                    f"by 1e-6 (seeds {SEED}+rank, +1), theta={args.theta}, eps={eps}, dt=2^-32")
     else:
         pos, vel, m = ics.plummer(args.n, SEED + rank)
         workload = (f"Plummer N={args.n} per GPU (virial units, seed {SEED}+rank), theta={args.theta}, "
@@ -417,7 +426,9 @@ def main():
     from paper_1106_1900_gb300 import autotune
 
     tuned = None if args.untuned else autotune.tuned_params(n, args.theta, args.workload)
-    kw = dict(tuned or {}, walk_split=int(args.split), mac=args.mac)
+    kw = dict(tuned or {}, walk_split=int(args.split), mac=args.mac, key_levels=args.key_levels)
+    if args.list_capacity:
+        kw["list_capacity"] = args.list_capacity
     tc = bh.TreeCode(n, device=local, **kw)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
@@ -428,7 +439,7 @@ def main():
         tc.set_state(P, V, M)
         tc.set_profiling(True)
         for _ in range(args.warmup):
-            tc.step(DT, args.theta, eps, graph=not args.eager)
+            tc.step(dt, args.theta, eps, graph=not args.eager)
         tc.check()
         torch.cuda.synchronize()
         tc.reset_counters()
@@ -444,7 +455,7 @@ def main():
                 if args.flush_mb > 0:
                     flush.fill_(k & 0xff)
                 ev[k][0].record(stream)
-                tc.step(DT, args.theta, eps, graph=not args.eager)
+                tc.step(dt, args.theta, eps, graph=not args.eager)
                 ev[k][1].record(stream)
                 ph = tc.phase_times()  # synchronises on this step's events
                 walk_ms.append(ph["walk"])
@@ -527,6 +538,7 @@ def main():
                    "params": "autotuned (paper_1106_1900_gb300/tuned.json)" if tuned else "paper defaults",
                    "cells": cnt["cells"], "groups": cnt["groups"], "graph": not args.eager,
                    "opening": "Eq. 1" if args.mac == 0 else "minimal distance",
+                   "key_levels": args.key_levels, "deepest_level": cnt["deepest"],
                    "walk": "split" if args.split else "fused"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak if peak else None, "traffic": traffic,

@@ -79,6 +79,15 @@ typedef struct bh_params {
                                (default); 1: the minimal-distance criterion (§2.3),
                                d > l/theta with d between the cell's cube and the
                                group's box (more interactions, smaller errors) */
+    int32_t key_levels;     /* key depth D in levels, 20..30 (App. B).  20 (default):
+                               the paper's 60-bit keys, trees at most 20 levels deep;
+                               a level-20 cell holding more than n_leaf bodies stays
+                               one leaf.  21..30: 3D-bit keys (a 60-bit word for
+                               levels 1..20 and a second word for 21..D), bodies
+                               quantised to 2^D cells per axis; the sort takes
+                               ceil(3(D-20)/8) more digit passes and the workspace
+                               24 B more per body.  Cells are identical to the 20-level
+                               tree wherever no level-20 cell exceeds n_leaf. */
 } bh_params;
 
 typedef struct bh_ctx bh_ctx; /* opaque, library-owned host object */
@@ -95,7 +104,7 @@ int bh_default_params(bh_params *p);
 
 /* Device workspace a context created with (p, n_max, n_sys_max) needs, in
  * bytes, written to *bytes.  The size grows linearly with n_max (cell table
- * bound 20*floor(n/(n_leaf+1)) + n + n_sys) plus the walk stacks
+ * bound D*floor(n/(n_leaf+1)) + n + n_sys, D = key_levels) plus the walk stacks
  * (SMs x resident warps x 2 x stack_capacity x 4 B) on `device`. */
 int bh_workspace_bytes(const bh_params *p, int64_t n_max, int32_t n_sys_max, int device, size_t *bytes);
 
@@ -210,8 +219,9 @@ int bh_get_counts(bh_ctx *ctx, int64_t out[9], void *stream);
 int bh_reset_counters(bh_ctx *ctx, void *stream);
 
 /* Exports the integer tree of the last build to host arrays (synchronises);
- * any pointer may be NULL.  Sorted order: skey[n] 60-bit Morton keys (a
- * forest orders by system, then key), perm[n] input index of each sorted
+ * any pointer may be NULL.  Sorted order: skey[n] 60-bit Morton keys, the
+ * levels 1..20 of each key (a forest orders by system, then key; deeper
+ * keys continue in bh_get_keys_lo), perm[n] input index of each sorted
  * body.  Cells (count from bh_get_counts) in (level, system, key) order:
  * level, pbeg, pend (sorted body range), parent (-1 at a root), first_child
  * (-1 at a leaf), n_children (0 at a leaf), is_leaf.  Groups in body order:
@@ -219,6 +229,13 @@ int bh_reset_counters(bh_ctx *ctx, void *stream);
 int bh_get_tree(bh_ctx *ctx, uint64_t *skey, int32_t *perm, int32_t *level, int32_t *pbeg, int32_t *pend,
                 int32_t *parent, int32_t *first_child, int32_t *n_children, int32_t *is_leaf, int32_t *gbeg,
                 int32_t *gend, void *stream);
+
+/* Exports the low key words of the last build in sorted order (synchronises):
+ * skey_lo[n] holds levels 21..D of each body's key (bit b of the low D-20
+ * bits of q_x, q_y, q_z at bits 3b, 3b+1, 3b+2), all zero for key_levels =
+ * 20; the full key is (skey << 3(D-20)) | skey_lo.  BH_ERR_INVALID_ARG for
+ * a NULL pointer, BH_ERR_STATE before a build. */
+int bh_get_keys_lo(bh_ctx *ctx, uint64_t *skey_lo, void *stream);
 
 /* Exports the moments of every cell (synchronises), any pointer may be NULL:
  * mass[C], com[C][3] (FP64, recombined from its two-float form), quad[C][6]

@@ -384,7 +384,8 @@ def block_level(acc, eps: float, eta: float, dt_max: float, k_max: int):
 class BlockState:
     """Block time-step state, bodies in the caller's order."""
 
-    def __init__(self, x, v, m, dt_max, k_max, eta, n_leaf=16, n_crit=64):
+    def __init__(self, x, v, m, dt_max, k_max, eta, n_leaf=16, n_crit=64, levels=LEVELS):
+        self.levels = _check_levels(levels)
         self.x = np.array(x, dtype=np.float64)
         self.v = np.array(v, dtype=np.float64)
         self.m = np.array(m, dtype=np.float64)
@@ -402,7 +403,7 @@ class BlockState:
 
 def block_start(st: BlockState, theta: float, eps: float):
     """Forces of every body at t = 0 and their first levels."""
-    a, pot, t, _ = tree_forces(st.x, st.m, theta, eps, st.n_leaf, st.n_crit)
+    a, pot, t, _ = tree_forces(st.x, st.m, theta, eps, st.n_leaf, st.n_crit, levels=st.levels)
     st.a, st.pot, st.tree = a, pot, t
     st.k = block_level(a, eps, st.eta, st.dt_max, st.k_max)
     return st
@@ -418,7 +419,7 @@ def block_step(st: BlockState, theta: float, eps: float, rebuild: bool = True, k
     d = ((T - st.t) * st.tick)[:, None]
     xp = st.x + st.v * d + 0.5 * st.a * d * d
     if rebuild or st.tree is None:
-        tr = build_tree(xp, st.m, st.n_leaf, st.n_crit)
+        tr = build_tree(xp, st.m, st.n_leaf, st.n_crit, levels=st.levels)
     else:
         tr = refresh_tree(st.tree, xp[st.tree.perm])
     st.tree = tr

@@ -103,6 +103,7 @@ class bh_params(ctypes.Structure):
         ("pool_per_body", ctypes.c_int32),
         ("walk_split", ctypes.c_int32),
         ("mac", ctypes.c_int32),
+        ("key_levels", ctypes.c_int32),
     ]
 
 
@@ -136,6 +137,7 @@ _SIG = {
     "bh_get_counts": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "bh_reset_counters": [ctypes.c_void_p, ctypes.c_void_p],
     "bh_get_tree": [ctypes.c_void_p] + [ctypes.c_void_p] * 11 + [ctypes.c_void_p],
+    "bh_get_keys_lo": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "bh_get_moments": [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_void_p],
     "bh_get_group_stats": [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_void_p],
     "bh_set_profiling": [ctypes.c_void_p, ctypes.c_int],
@@ -385,6 +387,9 @@ class TreeCode:
                  "gbeg", "gend")
         args = [out[k].ctypes.data_as(ctypes.c_void_p) for k in order]
         _check(self.lib.bh_get_tree(self.ctx, *args, _stream(stream)), "bh_get_tree")
+        out["skey_lo"] = np.zeros(n, np.uint64)
+        _check(self.lib.bh_get_keys_lo(self.ctx, out["skey_lo"].ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+               "bh_get_keys_lo")
         return out
 
     def moments(self, stream=None) -> dict:

@@ -13,7 +13,7 @@
 #include "bh_internal.cuh"
 
 namespace bh {
-int sort_passes_for(int S);
+int sort_passes_for(int S, int D);
 int64_t sort_tiles_for(int64_t n);
 }  // namespace bh
 
@@ -40,6 +40,7 @@ int validate_params(const bh_params *p) {
   if (p->list_capacity < 64 || p->pool_per_body < 1) return BH_ERR_INVALID_ARG;
   if (p->walk_split != 0 && p->walk_split != 1) return BH_ERR_INVALID_ARG;
   if (p->mac != 0 && p->mac != 1) return BH_ERR_INVALID_ARG;
+  if (p->key_levels < bh::kLevels || p->key_levels > bh::kLevelsMax) return BH_ERR_INVALID_ARG;
   return BH_OK;
 }
 
@@ -64,7 +65,8 @@ int plan(Ctx &c, const bh_params *p, int64_t n_max, int32_t s_max, int device) {
   c.device = device;
   c.n_max = n_max;
   c.s_max = s_max;
-  c.c_max = 20 * (n_max / (p->n_leaf + 1)) + n_max + s_max + 1;
+  c.levels = p->key_levels;
+  c.c_max = (int64_t)c.levels * (n_max / (p->n_leaf + 1)) + n_max + s_max + 1;
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return BH_ERR_CUDA;
   c.num_sms = prop.multiProcessorCount;
@@ -89,7 +91,7 @@ int plan(Ctx &c, const bh_params *p, int64_t n_max, int32_t s_max, int device) {
   c.trav_warps_total = (fused ? c.walk_grid : c.trav_grid) * bh::walk_block_warps();
   // the list pool serves the split walk only
   c.pool_cap = fused ? 32 : std::max<int64_t>((int64_t)p->pool_per_body * n_max, 1ll << 22);
-  c.sort_max_passes = bh::sort_passes_for(s_max);
+  c.sort_max_passes = bh::sort_passes_for(s_max, c.levels);
   c.sort_tiles_max = bh::sort_tiles_for(n_max);
   return BH_OK;
 }
@@ -98,7 +100,7 @@ void carve(Ctx &c, char *base, size_t *total) {
   Carver k{base};
   const size_t N = (size_t)c.n_max, S = (size_t)c.s_max, C = (size_t)c.c_max;
   const size_t W = (N + 31) / 32;
-  const size_t R = (size_t)bh::kRows * W;
+  const size_t R = (size_t)(c.levels + 2) * W;
   c.offs = k.take<int32_t>(S + 1);
   c.minmax = k.take<unsigned long long>(6 * S);
   c.frame = k.take<bh::Frame>(S);
@@ -109,6 +111,10 @@ void carve(Ctx &c, char *base, size_t *total) {
     c.key[b] = k.take<uint64_t>(N);
     c.idx[b] = k.take<uint32_t>(N);
   }
+  const bool deep = c.levels > bh::kLevels;
+  c.key_hi0 = deep ? k.take<uint64_t>(N) : nullptr;
+  c.key_lo0 = deep ? k.take<uint64_t>(N) : nullptr;
+  c.skey_lo = deep ? k.take<uint64_t>(N) : nullptr;
   c.part_hi = k.take<float4>(N);
   c.part_lo = k.take<float4>(N);
   c.lohi = k.take<uint8_t>(2 * N);
@@ -139,6 +145,7 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.c_link = k.take<int2>(C);
   c.c_mom = k.take<float4>(4 * C);
   c.c_mac = k.take<float4>(C);
+  c.c_mac_lo = deep ? k.take<float4>(C) : nullptr;
   c.g_beg = k.take<int32_t>(N + 1);
   c.g_sys = k.take<int32_t>(N);
   c.g_npc = k.take<int32_t>(N);
@@ -328,6 +335,7 @@ int bh_default_params(bh_params *p) {
   p->pool_per_body = 768;
   p->walk_split = 0;
   p->mac = 0;
+  p->key_levels = bh::kLevels;
   return BH_OK;
 }
 
@@ -761,11 +769,11 @@ int bh_get_counts(bh_ctx *ctx, int64_t out[9], void *stream) {
   int deepest = -1;
   if (c.n > 0 && c.built) {
     const size_t W = (size_t)(c.n + 31) / 32;
-    uint32_t starts[bh::kRows];
+    uint32_t starts[bh::kRowsMax];
     if ((rc = cu(cudaMemcpy2D(starts, sizeof(uint32_t), c.rowoff, W * sizeof(uint32_t), sizeof(uint32_t),
-                              bh::kRows, cudaMemcpyDeviceToHost))))
+                              c.levels + 2, cudaMemcpyDeviceToHost))))
       return rc;
-    for (int k = 0; k <= bh::kLevels; ++k) {
+    for (int k = 0; k <= c.levels; ++k) {
       uint32_t next = starts[k + 1];
       if (next > starts[k]) deepest = k;
     }
@@ -825,6 +833,22 @@ int bh_get_tree(bh_ctx *ctx, uint64_t *skey, int32_t *perm, int32_t *level, int3
   if ((rc = get(gbeg, c.g_beg, G * 4))) return rc;
   if ((rc = get(gend, c.g_beg + 1, G * 4))) return rc;
   return BH_OK;
+}
+
+int bh_get_keys_lo(bh_ctx *ctx, uint64_t *skey_lo, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.built) return BH_ERR_STATE;
+  if (!skey_lo) return BH_ERR_INVALID_ARG;
+  DeviceGuard g(c.device);
+  if ((rc = cu(cudaStreamSynchronize((cudaStream_t)stream)))) return rc;
+  const size_t n = (size_t)c.n;
+  if (!c.skey_lo) {
+    std::memset(skey_lo, 0, n * sizeof(uint64_t));
+    return BH_OK;
+  }
+  return n ? cu(cudaMemcpy(skey_lo, c.skey_lo, n * sizeof(uint64_t), cudaMemcpyDeviceToHost)) : BH_OK;
 }
 
 int bh_get_moments(bh_ctx *ctx, float *mass, double *com, float *quad, float *delta, float *size, void *stream) {

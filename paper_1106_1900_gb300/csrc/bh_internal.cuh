@@ -9,9 +9,9 @@
 
 namespace bh {
 
-constexpr int kLevels = 20;         // 60-bit keys, 20 levels below the root (App. B)
-constexpr int kRows = kLevels + 2;  // 21 cell levels + one row of group starts
-constexpr uint32_t kQMax = 1u << 20;
+constexpr int kLevels = 20;          // the 60-bit key word: levels 1..20 (App. B)
+constexpr int kLevelsMax = 30;       // deepest key: 90 bits, a second word for levels 21..30
+constexpr int kRowsMax = kLevelsMax + 2;  // cell levels 0..D + one row of group starts (<= 32)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCostBuckets = 256;  // logarithmic buckets of a group's estimated evaluation cost
 constexpr int kMaxCrit = 256;      // largest group size N_crit (the level build's window halo)
@@ -35,6 +35,7 @@ struct Ctx {
   int64_t n_max = 0;
   int32_t s_max = 1;
   int64_t c_max = 0;   // cell-table bound
+  int levels = kLevels;  // key depth D (bh_params.key_levels)
   int trav_grid = 0;   // persistent traversal blocks (split walk)
   int eval_grid = 0;   // persistent evaluation blocks (split walk)
   int walk_grid = 0;   // persistent blocks of the fused walk
@@ -68,8 +69,10 @@ struct Ctx {
   int32_t *sys_root;             // [S]
   uint32_t *frame_ticket;        // [1]
   // per body
-  uint64_t *key[2];
+  uint64_t *key[2];             // sort ping-pong; key[0] = the sorted 60-bit words (levels 1..20)
   uint32_t *idx[2];
+  uint64_t *key_hi0, *key_lo0;   // D > 20: both key words in input order
+  uint64_t *skey_lo;             // D > 20: the sorted low words (levels 21..D); else null
   float4 *part_hi, *part_lo;     // sorted bodies: (x_hi, y_hi, z_hi, m), (x_lo, y_lo, z_lo, 0)
   uint8_t *lohi;                 // [n][2] first level started, last level (leaf level)
   uint8_t *gstart;               // [n] group start flag
@@ -86,14 +89,15 @@ struct Ctx {
   double *h_pos, *h_mass;        // staging for bh_forces_host
   float *h_acc, *h_pot;
   // per warp of the level pass
-  uint32_t *rowcnt;              // [kRows][W]
-  uint32_t *rowoff;              // [kRows][W]
+  uint32_t *rowcnt;              // [D + 2][W]
+  uint32_t *rowoff;              // [D + 2][W]
   // per cell
   int32_t *c_level, *c_pbeg, *c_pend, *c_parent, *c_first, *c_nch;
   uint32_t *c_ctr;               // bottom-up arrival counters
   int2 *c_link;                  // walk link {first, count | leaf << 31}
   float4 *c_mom;                 // [C][4] moments (see k_moments.cu)
   float4 *c_mac;                 // [C] com_hi xyz, l/theta + delta
+  float4 *c_mac_lo;              // [C] key depth > 20: the low parts of c_mac's position; else null
   // per group
   int32_t *g_beg;                // [G+1]
   int32_t *g_sys;                // [G]
@@ -210,6 +214,16 @@ __device__ __forceinline__ int key_lcp(uint64_t a, uint64_t b) {
   if (x == 0) return kLevels;
   int h = 63 - __clzll((long long)x);
   return (59 - h) / 3;
+}
+
+// Common prefix of two keys of D levels stored as (60-bit word, low word of
+// 3 (D - 20) bits), in levels (0..D).
+__device__ __forceinline__ int key_lcp2(uint64_t ha, uint64_t la, uint64_t hb, uint64_t lb, int D) {
+  if (ha != hb) return key_lcp(ha, hb);
+  const uint64_t x = la ^ lb;
+  if (x == 0) return D;
+  const int h = 63 - __clzll((long long)x);
+  return kLevels + (3 * (D - kLevels) - 1 - h) / 3;
 }
 
 // Keep the low 20 bits of v, bit b moved to bit 3b (a 60-bit spread).

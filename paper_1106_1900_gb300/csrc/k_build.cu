@@ -1,11 +1,15 @@
 // k_build.cu -- tree construction on the GPU (§2.1, App. A, App. B).
 //
 //  frame + keys   per-system bounding box (order-preserving 64-bit atomics),
-//                 frame (origin, power-of-two side L), 60-bit Morton keys.
+//                 frame (origin, power-of-two side L), 60-bit Morton keys;
+//                 with a key depth D > 20 (App. B: longer keys lift the
+//                 20-level limit) a second word holds levels 21..D.
 //  sort           stable LSD radix sort of (key, index), 8-bit digits, one
 //                 upsweep histogram for all passes and one pass kernel per
 //                 digit with decoupled look-back (bounded waits).  A forest
 //                 adds digits of the system id as the most significant ones.
+//                 Deeper keys sort their low word first, then gather the
+//                 60-bit word into the current order and sort by it.
 //  move           gather of the bodies into key order, split into two floats.
 //  cells          the paper's level loop (mask keys of unfinished bodies,
 //                 group equal masked keys, cells of <= N_leaf bodies become
@@ -175,41 +179,58 @@ __global__ void __launch_bounds__(kBlock) k_bbox(const double *__restrict__ pos,
 }
 
 // ----------------------------------------------------------------- keys
-// floor(d * 2^k) clamped to [0, 2^20 - 1], from the bits of d: a product with a
+// floor(d * 2^k) clamped to [0, qmax], from the bits of d: a product with a
 // power of two is exact (or, below 2^-1022, under 1 anyway), so this equals
 // clamp(floor(__dmul_rn(d, 2^k))) without FP64 arithmetic.  NaN gives 0.
-__device__ __forceinline__ uint32_t quantize(double d, int k) {
+__device__ __forceinline__ uint32_t quantize(double d, int k, uint32_t qmax) {
   const long long b = __double_as_longlong(d);
   if (b <= 0) return 0;  // negative, -0 or +0
   const int e = (int)((b >> 52) & 0x7ff);
   const unsigned long long frac = (unsigned long long)b & ((1ull << 52) - 1);
-  if (e == 0x7ff) return frac ? 0u : kQMax - 1;  // NaN, +inf
+  if (e == 0x7ff) return frac ? 0u : qmax;  // NaN, +inf
   // d = m 2^(e' - 1075) with the hidden bit (normal) or e' = 1 (subnormal)
   const unsigned long long m = e ? (frac | (1ull << 52)) : frac;
   const int sh = 1075 - (e ? e : 1) - k;  // d 2^k = m 2^-sh
-  if (sh <= 0) return kQMax - 1;          // >= 2^52
+  if (sh <= 0) return qmax;               // >= 2^52
   if (sh >= 64) return 0;
   const unsigned long long t = m >> sh;
-  return t >= kQMax ? kQMax - 1 : (uint32_t)t;
+  return t >= qmax ? qmax : (uint32_t)t;
 }
 
-template <bool FOREST>
+// Keys of D levels: q = floor((x - origin) 2^D / L) per axis; the 60-bit word
+// interleaves the top 20 bits of q (levels 1..20), the low word (DEEP) the
+// remaining D - 20 bits.  DEEP writes both words in input order and the low
+// one also into the sort's first buffer.
+template <bool FOREST, bool DEEP>
 __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos, int n,
                                                  const int32_t *__restrict__ offs, int S,
-                                                 const Frame *__restrict__ frame, uint64_t *__restrict__ key,
+                                                 const Frame *__restrict__ frame, int D, uint64_t *__restrict__ key,
+                                                 uint64_t *__restrict__ key_hi0, uint64_t *__restrict__ key_lo0,
                                                  uint32_t *__restrict__ idx) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = FOREST ? sys_of(offs, S, i) : 0;
   Frame f = frame[s];
-  // scale = 2^20 / L = 2^k exactly (L is a power of two, possibly subnormal)
+  const int DD = DEEP ? D : kLevels;
+  // scale = 2^D / L = 2^k exactly (L is a power of two, possibly subnormal)
   const unsigned long long lb = (unsigned long long)__double_as_longlong(f.w);
   const int le = (int)((lb >> 52) & 0x7ffull);
-  const int k = 20 - (le ? le - 1023 : -1074 + (63 - __clzll((long long)lb)));
+  const int k = DD - (le ? le - 1023 : -1074 + (63 - __clzll((long long)lb)));
   double o[3] = {f.x, f.y, f.z};
   uint32_t q[3];
-  for (int a = 0; a < 3; ++a) q[a] = quantize(__dsub_rn(pos[3 * (size_t)i + a], o[a]), k);
-  key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  const uint32_t qmax = (1u << DD) - 1u;
+  for (int a = 0; a < 3; ++a) q[a] = quantize(__dsub_rn(pos[3 * (size_t)i + a], o[a]), k, qmax);
+  if (!DEEP) {
+    key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+  } else {
+    const int sl = DD - kLevels;
+    const uint32_t ml = (1u << sl) - 1u;
+    const uint64_t hi = spread3(q[0] >> sl) | (spread3(q[1] >> sl) << 1) | (spread3(q[2] >> sl) << 2);
+    const uint64_t lo = spread3(q[0] & ml) | (spread3(q[1] & ml) << 1) | (spread3(q[2] & ml) << 2);
+    key_hi0[i] = hi;
+    key_lo0[i] = lo;
+    key[i] = lo;
+  }
   idx[i] = (uint32_t)i;
 }
 
@@ -220,22 +241,34 @@ constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 3
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookback = 8;  // predecessor tiles read per look-back step
 
-__device__ __forceinline__ uint32_t sort_digit(uint64_t k, uint32_t v, int pass, int key_passes,
-                                               const int32_t *offs, int S) {
-  if (pass < key_passes) return (uint32_t)(k >> (8 * pass)) & 0xffu;
-  return ((uint32_t)sys_of(offs, S, (int)v) >> (8 * (pass - key_passes))) & 0xffu;
+// Digit of a pass: byte `byte` of the key word, or (byte < 0) byte -1 - byte
+// of the body's system id.
+__device__ __forceinline__ uint32_t sort_digit(uint64_t k, uint32_t v, int byte, const int32_t *offs, int S) {
+  if (byte >= 0) return (uint32_t)(k >> (8 * byte)) & 0xffu;
+  return ((uint32_t)sys_of(offs, S, (int)v) >> (8 * (-1 - byte))) & 0xffu;
 }
 
-// All digit histograms in one read of the keys.
-__global__ void __launch_bounds__(kBlock) k_sort_hist(const uint64_t *__restrict__ key, int n, int passes,
-                                                      int key_passes, const int32_t *__restrict__ offs, int S,
+// Byte of pass p: passes 0..lo_passes-1 take the low key word, the next 8 the
+// 60-bit word, the rest the system id.
+__host__ __device__ __forceinline__ int pass_byte(int p, int lo_passes) {
+  if (p < lo_passes) return p;
+  if (p < lo_passes + 8) return p - lo_passes;
+  return -1 - (p - lo_passes - 8);
+}
+
+// All digit histograms in one read of the key words (a histogram does not
+// depend on the order, so both words are read in input order).
+__global__ void __launch_bounds__(kBlock) k_sort_hist(const uint64_t *__restrict__ klo,
+                                                      const uint64_t *__restrict__ khi, int n, int lo_passes,
+                                                      int passes, const int32_t *__restrict__ offs, int S,
                                                       uint32_t *hist) {
   extern __shared__ uint32_t s_h[];  // [passes][256]
   for (int t = threadIdx.x; t < passes * 256; t += blockDim.x) s_h[t] = 0;
   __syncthreads();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint64_t k = key[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&s_h[p * 256 + sort_digit(k, (uint32_t)i, p, key_passes, offs, S)], 1u);
+    const uint64_t h = khi[i], l = lo_passes ? klo[i] : 0;
+    for (int p = 0; p < passes; ++p)
+      atomicAdd(&s_h[p * 256 + sort_digit(p < lo_passes ? l : h, (uint32_t)i, pass_byte(p, lo_passes), offs, S)], 1u);
   }
   __syncthreads();
   for (int t = threadIdx.x; t < passes * 256; t += blockDim.x)
@@ -289,7 +322,7 @@ __device__ __forceinline__ uint32_t block256_exclusive(uint32_t v, uint32_t *s_w
 // digit counts, then sums its predecessors' (bounded wait), then scatters.
 __global__ void __launch_bounds__(kBlock) k_sort_pass(const uint64_t *__restrict__ kin,
                                                       const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                                                      uint32_t *__restrict__ vout, int n, int pass, int key_passes,
+                                                      uint32_t *__restrict__ vout, int n, int byte,
                                                       const uint32_t *__restrict__ binbase, uint32_t *status,
                                                       uint32_t *tile_ctr, const int32_t *__restrict__ offs, int S,
                                                       int32_t *err) {
@@ -320,7 +353,7 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(const uint64_t *__restrict
     bool ok = e < n;
     k[j] = ok ? kin[e] : 0;
     v[j] = ok ? vin[e] : 0;
-    d[j] = ok ? sort_digit(k[j], v[j], pass, key_passes, offs, S) : 256u;
+    d[j] = ok ? sort_digit(k[j], v[j], byte, offs, S) : 256u;
   }
 #pragma unroll
   for (int j = 0; j < kSortIpt; ++j) {
@@ -402,6 +435,14 @@ __global__ void __launch_bounds__(kBlock) k_sort_pass(const uint64_t *__restrict
   }
 }
 
+// dst[j] = src[idx[j]]: a key word in the order of the index array.
+__global__ void __launch_bounds__(kBlock) k_gather_key(const uint32_t *__restrict__ idx,
+                                                       const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
+                                                       int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) dst[j] = src[idx[j]];
+}
+
 // ----------------------------------------------------------------- move
 __global__ void __launch_bounds__(kBlock) k_move(const double *__restrict__ pos, const double *__restrict__ mass,
                                                  const uint32_t *__restrict__ perm, int n, float4 *part_hi,
@@ -445,12 +486,20 @@ constexpr int kHalo = kMaxCrit;  // >= N_crit >= N_leaf
 
 // Per body: first level it starts a cell at (common prefix with the previous
 // key + 1), its leaf level, whether it starts a group; per warp: how many
-// cells it starts at each level and how many groups.
-template <bool FOREST>
-__global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ skey, int n,
+// cells it starts at each level and how many groups.  DEEP: keys of D > 20
+// levels, the low words in skey_lo.
+template <bool FOREST, bool DEEP>
+__global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ skey,
+                                                   const uint64_t *__restrict__ skey_lo, int D, int n,
                                                    const int32_t *__restrict__ offs, int S, int n_leaf, int n_crit,
                                                    uint8_t *lohi, uint8_t *gstart, uint32_t *rowcnt, int W) {
+  const int DD = DEEP ? D : kLevels;
   __shared__ uint64_t s_key[kBlock + 2 * kHalo];
+  __shared__ uint64_t s_klo[DEEP ? kBlock + 2 * kHalo : 1];
+  // common prefix (levels) of the keys at shared positions a and b
+  auto lcp = [&](int a, int b) -> int {
+    return DEEP ? key_lcp2(s_key[a], s_klo[a], s_key[b], s_klo[b], DD) : key_lcp(s_key[a], s_key[b]);
+  };
   __shared__ int8_t s_wl[kBlock + kHalo];  // lcp of windows of N_leaf + 1 keys starting at b0 - kHalo + t
   __shared__ int8_t s_wc[kBlock + kHalo];  // lcp of windows of N_crit + 1 keys
   __shared__ int8_t s_tl[kBlock + kHalo], s_tc[kBlock + kHalo];  // doubling buffers
@@ -458,6 +507,7 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
   for (int t = threadIdx.x; t < kBlock + 2 * kHalo; t += kBlock) {
     int i = b0 - kHalo + t;
     s_key[t] = (i >= 0 && i < n) ? skey[i] : 0;
+    if (DEEP) s_klo[t] = (i >= 0 && i < n) ? skey_lo[i] : 0;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < kBlock + kHalo; t += kBlock) {
@@ -471,8 +521,8 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
         se = offs[s + 1];
       }
       (void)sb;
-      if (s0 + n_leaf < se) wl = (int8_t)key_lcp(s_key[t], s_key[t + n_leaf]);
-      if (s0 + n_crit < se) wc = (int8_t)key_lcp(s_key[t], s_key[t + n_crit]);
+      if (s0 + n_leaf < se) wl = (int8_t)lcp(t, t + n_leaf);
+      if (s0 + n_crit < se) wc = (int8_t)lcp(t, t + n_crit);
     }
     s_wl[t] = wl;
     s_wc[t] = wc;
@@ -509,24 +559,25 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
     int sb = 0;
     if (FOREST) sb = offs[sys_of(offs, S, i)];
     const int t = threadIdx.x + kHalo;  // position of i in s_key
-    int prev = (i > sb) ? key_lcp(s_key[t - 1], s_key[t]) : -1;
+    int prev = (i > sb) ? lcp(t - 1, t) : -1;
     // windows of N+1 keys starting at i-N .. i (a window's lcp is -1 where it
     // leaves the system, so windows starting before the system's first body count nothing)
     const int wl = max((int)al[t - n_leaf], (int)al[t + 1 - (1 << jl)]);
     const int wc = max((int)ac[t - n_crit], (int)ac[t + 1 - (1 << jc)]);
-    int lam = min(wl + 1, kLevels);
-    int mu = wc + 1;  // 21: even the level-20 cell holds more than N_crit bodies
+    int lam = min(wl + 1, DD);
+    int mu = wc + 1;  // D + 1: even the level-D cell holds more than N_crit bodies
     lo = prev + 1;
     hi = lam;
     if (mu <= lam) {
       gs = (lo <= mu);
     } else {
-      // chunks of N_crit inside a level-20 leaf: find the start of the run of equal keys
-      uint64_t kk = s_key[t];
-      int a = sb, b = i;  // first index in [a, b] with key == kk
+      // chunks of N_crit inside a level-D leaf: find the start of the run of equal keys
+      const uint64_t kk = s_key[t], kl = DEEP ? s_klo[t] : 0;
+      int a = sb, b = i;  // first index in [a, b] with key == (kk, kl)
       while (a < b) {
         int mid = (a + b) >> 1;
-        if (skey[mid] < kk) a = mid + 1; else b = mid;
+        const uint64_t h = skey[mid];
+        if (h < kk || (DEEP && h == kk && skey_lo[mid] < kl)) a = mid + 1; else b = mid;
       }
       gs = ((i - a) % n_crit) == 0;
     }
@@ -538,19 +589,20 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
   const int w = i >> 5;
   uint32_t mine = 0;
 #pragma unroll
-  for (int k = 0; k <= kLevels; ++k) {
+  for (int k = 0; k <= (DEEP ? kLevelsMax : kLevels); ++k) {
+    if (DEEP && k > DD) break;
     unsigned b = __ballot_sync(kFull, ok && lo <= k && k <= hi);
     if (lane == k) mine = __popc(b);
   }
   unsigned bg = __ballot_sync(kFull, ok && gs);
-  if (lane == kRows - 1) mine = __popc(bg);
-  if (lane < kRows && w < W) rowcnt[(size_t)lane * W + w] = mine;
+  if (lane == DD + 1) mine = __popc(bg);  // rows 0..D: cells per level; row D + 1: groups
+  if (lane < DD + 2 && w < W) rowcnt[(size_t)lane * W + w] = mine;
 }
 
 // Writes every cell (level, leaf flag, first body, parent/first child where
 // the same body starts both) and every group start.
-template <bool FOREST>
-__global__ void __launch_bounds__(kBlock) k_emit(int n, const int32_t *__restrict__ offs, int S,
+template <bool FOREST, bool DEEP>
+__global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__restrict__ offs, int S,
                                                  const uint8_t *__restrict__ lohi, const uint8_t *__restrict__ gstart,
                                                  const uint32_t *__restrict__ rowoff, int W,
                                                  const uint64_t *__restrict__ scan_total, int32_t *c_level,
@@ -568,9 +620,10 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, const int32_t *__restric
     gs = gstart[i];
     if (FOREST) s = sys_of(offs, S, i);
   }
-  const uint32_t C = rowoff[(size_t)(kRows - 1) * W];
+  const int DD = DEEP ? D : kLevels;
+  const uint32_t C = rowoff[(size_t)(DD + 1) * W];
   int prev = -1;
-  for (int k = 0; k <= kLevels; ++k) {
+  for (int k = 0; k <= DD; ++k) {
     bool in = ok && lo <= k && k <= hi;
     unsigned b = __ballot_sync(kFull, in);
     if (b == 0) continue;
@@ -589,7 +642,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, const int32_t *__restric
   }
   unsigned bg = __ballot_sync(kFull, ok && gs);
   if (ok && gs) {
-    int g = (int)(rowoff[(size_t)(kRows - 1) * W + w] - C + __popc(bg & lt));
+    int g = (int)(rowoff[(size_t)(DD + 1) * W + w] - C + __popc(bg & lt));
     g_beg[g] = i;
     g_sys[g] = s;
   }
@@ -604,8 +657,9 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, const int32_t *__restric
 // One thread per cell: body range end (galloping search in the sorted keys),
 // parent (binary search among the cells one level up), number of children
 // (binary search among the cells one level down) and the walk's link word.
-template <bool FOREST>
+template <bool FOREST, bool DEEP>
 __global__ void __launch_bounds__(kBlock) k_link(int n, const uint64_t *__restrict__ skey,
+                                                 const uint64_t *__restrict__ skey_lo, int D,
                                                  const int32_t *__restrict__ offs, int S,
                                                  const uint32_t *__restrict__ rowoff, int W,
                                                  const int32_t *__restrict__ counts, int32_t *c_level,
@@ -622,17 +676,22 @@ __global__ void __launch_bounds__(kBlock) k_link(int n, const uint64_t *__restri
     if (FOREST) se = offs[sys_of(offs, S, i) + 1];
     int pend = se;
     if (k > 0) {
-      const int sh = 60 - 3 * k;
-      const uint64_t P = skey[i] >> sh;
+      // does body j share body i's level-k prefix?
+      const bool low = DEEP && k > kLevels;  // the prefix reaches into the low word
+      const int sh = low ? 3 * (D - k) : 60 - 3 * k;
+      const uint64_t P = low ? skey_lo[i] >> sh : skey[i] >> sh, H = skey[i];
+      auto same = [&](int j) -> bool {
+        return low ? (skey[j] == H && (skey_lo[j] >> sh) == P) : (skey[j] >> sh) == P;
+      };
       int in_run = i, step = 1;
-      while (i + step < se && (skey[i + step] >> sh) == P) {
+      while (i + step < se && same(i + step)) {
         in_run = i + step;
         step <<= 1;
       }
       int a = in_run + 1, b = min(i + step, se);  // first index with another prefix lies in [a, b]
       while (a < b) {
         int mid = (a + b) >> 1;
-        if ((skey[mid] >> sh) == P) a = mid + 1; else b = mid;
+        if (same(mid)) a = mid + 1; else b = mid;
       }
       pend = a;
     }
@@ -779,10 +838,22 @@ cudaError_t launch_frame_keys(Ctx &c, const double *pos, const double *mass, cud
   else
     k_bbox<false><<<nb, kBlock, 0, s>>>(pos, mass, n, c.offs, c.n_sys, c.minmax, c.frame_ticket, c.frame,
                                         c.framef, c.d_status);
-  if (forest)
-    k_keys<true><<<cdiv(n, kBlock), kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, c.key[0], c.idx[0]);
-  else
-    k_keys<false><<<cdiv(n, kBlock), kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, c.key[0], c.idx[0]);
+  const int D = c.levels, kb = cdiv(n, kBlock);
+  if (D > kLevels) {
+    if (forest)
+      k_keys<true, true><<<kb, kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, D, c.key[0], c.key_hi0, c.key_lo0,
+                                               c.idx[0]);
+    else
+      k_keys<false, true><<<kb, kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, D, c.key[0], c.key_hi0, c.key_lo0,
+                                                c.idx[0]);
+  } else {
+    if (forest)
+      k_keys<true, false><<<kb, kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, D, c.key[0], nullptr, nullptr,
+                                                c.idx[0]);
+    else
+      k_keys<false, false><<<kb, kBlock, 0, s>>>(pos, n, c.offs, c.n_sys, c.frame, D, c.key[0], nullptr, nullptr,
+                                                 c.idx[0]);
+  }
   c.launches += 2;
   return cudaGetLastError();
 }
@@ -794,7 +865,10 @@ static int sort_sys_passes(int S) {
   return (bits + 7) / 8;
 }
 
-int sort_passes_for(int S) { return 8 + sort_sys_passes(S); }
+// Digit passes over the low key word of a D-level key (0 for D = 20).
+static int sort_lo_passes(int D) { return D > kLevels ? (3 * (D - kLevels) + 7) / 8 : 0; }
+
+int sort_passes_for(int S, int D) { return sort_lo_passes(D) + 8 + sort_sys_passes(S); }
 
 cudaError_t build_init_attrs() {
   return cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -804,8 +878,9 @@ int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 
 cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
   const int n = (int)c.n;
-  const int key_passes = 8;
-  const int passes = key_passes + sort_sys_passes(c.n_sys);
+  const bool deep = c.levels > kLevels;
+  const int lo_passes = sort_lo_passes(c.levels);
+  const int passes = sort_passes_for(c.n_sys, c.levels);
   const int tiles = cdiv(n, kSortTile);
   cudaError_t e;
   e = cudaMemsetAsync(c.sort_hist, 0, sizeof(uint32_t) * passes * 256, s);
@@ -815,15 +890,21 @@ cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
   e = cudaMemsetAsync(c.sort_tile_ctr, 0, sizeof(uint32_t) * passes, s);
   if (e) return e;
   int hb = min(cdiv(n, kBlock), c.num_sms * 4);
-  k_sort_hist<<<hb, kBlock, sizeof(uint32_t) * passes * 256, s>>>(c.key[0], n, passes, key_passes, c.offs,
-                                                                   c.n_sys, c.sort_hist);
+  k_sort_hist<<<hb, kBlock, sizeof(uint32_t) * passes * 256, s>>>(deep ? c.key_lo0 : nullptr,
+                                                                   deep ? c.key_hi0 : c.key[0], n, lo_passes, passes,
+                                                                   c.offs, c.n_sys, c.sort_hist);
   k_sort_binscan<<<passes, 256, 0, s>>>(c.sort_hist);
   const size_t dyn = (size_t)kSortTile * (8 + 4 + 1);
   for (int p = 0; p < passes; ++p) {
     int src = p & 1;
-    k_sort_pass<<<tiles, kBlock, dyn, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1], n, p, key_passes,
-                                           c.sort_hist + p * 256, c.sort_status + (size_t)p * tiles * 256,
-                                           c.sort_tile_ctr + p, c.offs, c.n_sys, c.d_status);
+    if (deep && p == lo_passes) {  // sorted by the low word: bring the 60-bit word into this order
+      k_gather_key<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.idx[src], c.key_hi0, c.key[src], n);
+      c.launches++;
+    }
+    k_sort_pass<<<tiles, kBlock, dyn, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1], n,
+                                           pass_byte(p, lo_passes), c.sort_hist + p * 256,
+                                           c.sort_status + (size_t)p * tiles * 256, c.sort_tile_ctr + p, c.offs,
+                                           c.n_sys, c.d_status);
   }
   c.launches += 2 + passes;
   if (passes & 1) {  // 9 passes (forest of 2..256 systems): bring the result back to buffer 0
@@ -831,6 +912,10 @@ cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
     if (e) return e;
     e = cudaMemcpyAsync(c.idx[0], c.idx[1], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
     if (e) return e;
+  }
+  if (deep) {  // the low words in the final order
+    k_gather_key<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.idx[0], c.key_lo0, c.skey_lo, n);
+    c.launches++;
   }
   return cudaGetLastError();
 }
@@ -880,37 +965,30 @@ cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, ui
 
 int64_t scan_blocks_for(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
-cudaError_t launch_cells(Ctx &c, cudaStream_t s) {
-  const int n = (int)c.n;
+template <bool FOREST, bool DEEP>
+static cudaError_t cells_impl(Ctx &c, cudaStream_t s) {
+  const int n = (int)c.n, D = c.levels;
   const int W = cdiv(n, 32);
-  const bool forest = c.n_sys > 1;
   const int nb = cdiv(n, kBlock);
-  if (forest)
-    k_levels<true><<<nb, kBlock, 0, s>>>(c.key[0], n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit, c.lohi, c.gstart,
-                                         c.rowcnt, W);
-  else
-    k_levels<false><<<nb, kBlock, 0, s>>>(c.key[0], n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit, c.lohi, c.gstart,
-                                          c.rowcnt, W);
+  k_levels<FOREST, DEEP><<<nb, kBlock, 0, s>>>(c.key[0], c.skey_lo, D, n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit,
+                                               c.lohi, c.gstart, c.rowcnt, W);
   c.launches++;
-  cudaError_t e = launch_scan_u32(c, c.rowcnt, c.rowoff, (int64_t)kRows * W, s);
+  cudaError_t e = launch_scan_u32(c, c.rowcnt, c.rowoff, (int64_t)(D + 2) * W, s);
   if (e) return e;
-  if (forest)
-    k_emit<true><<<nb, kBlock, 0, s>>>(n, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total, c.c_level,
-                                       c.c_pbeg, c.c_parent, c.c_first, c.c_ctr, c.sys_root, c.g_beg, c.g_sys,
-                                       c.d_counts);
-  else
-    k_emit<false><<<nb, kBlock, 0, s>>>(n, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total, c.c_level,
-                                        c.c_pbeg, c.c_parent, c.c_first, c.c_ctr, c.sys_root, c.g_beg, c.g_sys,
-                                        c.d_counts);
-  const int lb = c.num_sms * 8;
-  if (forest)
-    k_link<true><<<lb, kBlock, 0, s>>>(n, c.key[0], c.offs, c.n_sys, c.rowoff, W, c.d_counts, c.c_level, c.c_pbeg,
-                                       c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_link);
-  else
-    k_link<false><<<lb, kBlock, 0, s>>>(n, c.key[0], c.offs, c.n_sys, c.rowoff, W, c.d_counts, c.c_level, c.c_pbeg,
-                                        c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_link);
+  k_emit<FOREST, DEEP><<<nb, kBlock, 0, s>>>(n, D, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total,
+                                             c.c_level, c.c_pbeg, c.c_parent, c.c_first, c.c_ctr, c.sys_root,
+                                             c.g_beg, c.g_sys, c.d_counts);
+  k_link<FOREST, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(n, c.key[0], c.skey_lo, D, c.offs, c.n_sys, c.rowoff, W,
+                                                        c.d_counts, c.c_level, c.c_pbeg, c.c_pend, c.c_parent,
+                                                        c.c_first, c.c_nch, c.c_link);
   c.launches += 2;
   return cudaGetLastError();
+}
+
+cudaError_t launch_cells(Ctx &c, cudaStream_t s) {
+  const bool forest = c.n_sys > 1, deep = c.levels > kLevels;
+  if (forest) return deep ? cells_impl<true, true>(c, s) : cells_impl<true, false>(c, s);
+  return deep ? cells_impl<false, true>(c, s) : cells_impl<false, false>(c, s);
 }
 
 }  // namespace bh

@@ -39,6 +39,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// s + c += v, the rounding error of s + v kept in c (TwoSum)
+__device__ __forceinline__ void add_compensated(float &s, float &c, float v) {
+  float t, e;
+  two_sum(s, v, t, e);
+  s = t;
+  c += e;
+}
+
 // (hi, lo) -> the same sum with hi the rounded value and |lo| <= ulp(hi)/2
 // (TwoSum: exact whatever the magnitudes).  The walk reads the high part alone
 // (the opening test), so it must be the correctly rounded value.
@@ -49,22 +57,39 @@ __device__ __forceinline__ void renormalise(float &hi, float &lo) {
   lo = e;
 }
 
+// Key words of the sorted bodies: the 60-bit word (levels 1..20) and, for a
+// key depth D > 20, the low word (levels 21..D).
+struct Keys {
+  const uint64_t *__restrict__ hi;
+  const uint64_t *__restrict__ lo;
+  int D;
+};
+
+// Integer corner along axis a of the level-k cell holding sorted body i: the
+// top k bits of the body's quantised coordinate (k <= D).
+template <bool DEEP>
+__device__ __forceinline__ uint32_t cell_corner(const Keys &K, int k, int i, int a) {
+  if (k == 0) return 0u;
+  const uint32_t top = compact3(K.hi[i] >> a);  // levels 1..20
+  if (!DEEP || k <= kLevels) return top >> (kLevels - k);
+  return (top << (k - kLevels)) | (compact3(K.lo[i] >> a) >> (K.D - k));
+}
+
 // Geometric centre origin + (i + 1/2) l of the level-k cell holding sorted
 // body i, l = L 2^-k.  In FP32 when the frame allows: (i + 1/2) l is exact
-// (i < 2^20, l a power of two) and TwoSum adds it to the origin's float pair;
-// otherwise (a side below 2^-100 or above 2^100) in FP64.
-template <bool FOREST>
-__device__ __forceinline__ Centre cell_centre(int k, int i, const uint64_t *__restrict__ skey,
-                                              const int32_t *__restrict__ offs, int S,
+// (i < 2^23, l a power of two) and TwoSum adds it to the origin's float pair;
+// otherwise (a side below 2^-100 or above 2^100, or a cell below level 23 of
+// a deeper key) in FP64, where (i + 1/2) l is exact for i < 2^30.
+template <bool FOREST, bool DEEP>
+__device__ __forceinline__ Centre cell_centre(int k, int i, const Keys &K, const int32_t *__restrict__ offs, int S,
                                               const Frame *__restrict__ frame, const FrameF *__restrict__ framef) {
   const int s = FOREST ? sys_of(offs, S, i) : 0;
   const FrameF f = framef[s];
-  const uint64_t key = skey[i];
   Centre C;
-  if (f.L > 0x1p-100f && f.L < 0x1p100f) {
+  if (f.L > 0x1p-100f && f.L < 0x1p100f && (!DEEP || k <= 23)) {
     const float l = ldexpf(f.L, -k);
     for (int a = 0; a < 3; ++a) {
-      const uint32_t corner = (k == 0) ? 0u : (compact3(key >> a) >> (kLevels - k));
+      const uint32_t corner = cell_corner<DEEP>(K, k, i, a);
       float e;
       two_sum(f.ohi[a], ((float)corner + 0.5f) * l, C.hi[a], e);
       C.lo[a] = e + f.olo[a];
@@ -76,7 +101,7 @@ __device__ __forceinline__ Centre cell_centre(int k, int i, const uint64_t *__re
     const double l = ldexp(g.w, -k);
     const double o[3] = {g.x, g.y, g.z};
     for (int a = 0; a < 3; ++a) {
-      const uint32_t corner = (k == 0) ? 0u : (compact3(key >> a) >> (kLevels - k));
+      const uint32_t corner = cell_corner<DEEP>(K, k, i, a);
       split2(__dadd_rn(o[a], __dmul_rn((double)corner + 0.5, l)), C.hi[a], C.lo[a]);
     }
     C.l = (float)l;
@@ -115,9 +140,8 @@ __device__ __forceinline__ void add_point_quad(float Q[6], float m, float dx, fl
 // cell keeps its geometric centre and its size grows to the smallest cube
 // about that centre holding its bodies (a leaf) or its children's cubes (a
 // node, l/2 + the largest child side), never below its built size.
-template <bool FOREST, bool REFRESH>
-__global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__ skey,
-                                                    const int32_t *__restrict__ offs, int S,
+template <bool FOREST, bool REFRESH, bool DEEP>
+__global__ void __launch_bounds__(kBlock) k_moments(const Keys K, const int32_t *__restrict__ offs, int S,
                                                     const Frame *__restrict__ frame,
                                                     const FrameF *__restrict__ framef,
                                                     const int32_t *__restrict__ counts,
@@ -136,19 +160,27 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
     // ---- leaf: from its bodies
     {
       const int k = lv & 31, b = c_pbeg[c], e = c_pend[c];
-      Centre G = cell_centre<FOREST>(k, b, skey, offs, S, frame, framef);
+      Centre G = cell_centre<FOREST, DEEP>(k, b, K, offs, S, frame, framef);
+      // compensated sums (TwoSum): a leaf at the deepest level may hold
+      // thousands of bodies, whose plain FP32 sum of equal masses drifts by
+      // ~n ulp
       float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, ext = 0.f;
+      float eM = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
       for (int i = b; i < e; ++i) {
         float4 h = part_hi[i], l = part_lo[i];
         float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]);
         float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]);
         float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]);
         if (REFRESH) ext = fmaxf(ext, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
-        M += h.w;
-        sx += h.w * dx;
-        sy += h.w * dy;
-        sz += h.w * dz;
+        add_compensated(M, eM, h.w);
+        add_compensated(sx, ex, h.w * dx);
+        add_compensated(sy, ey, h.w * dy);
+        add_compensated(sz, ez, h.w * dz);
       }
+      M += eM;
+      sx += ex;
+      sy += ey;
+      sz += ez;
       float cm[3] = {0.f, 0.f, 0.f};
       if (M > 0.f) {
         cm[0] = sx / M;
@@ -167,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
     }
     // ---- climb while this thread is the last child to arrive
     int cur = c;
-    for (int climb = 0; climb <= kLevels; ++climb) {  // at most 20 ancestors
+    for (int climb = 0; climb <= kLevelsMax; ++climb) {  // at most D ancestors
       const int p = c_parent[cur];
       if (p < 0 || p >= C) break;
       __threadfence();
@@ -176,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
       if (atomicAdd(&c_ctr[p], 1u) != nch - 1) break;
       __threadfence();
       const int k = c_level[p] & 31;
-      Centre G = cell_centre<FOREST>(k, c_pbeg[p], skey, offs, S, frame, framef);
+      Centre G = cell_centre<FOREST, DEEP>(k, c_pbeg[p], K, offs, S, frame, framef);
       const int f = c_first[p];
       float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, lch = 0.f;
       for (uint32_t j = 0; j < nch; ++j) {
@@ -221,9 +253,11 @@ __global__ void __launch_bounds__(kBlock) k_moments(const uint64_t *__restrict__
 }
 
 // Opening radius of Eq. 1 for this theta: r_open = l/theta + delta, beside the
-// centre of mass (high part) that the walk's opening test reads.
+// centre of mass (high part) that the walk's opening test reads; with keys
+// deeper than 20 levels also the low part (mac_lo non-null), since a cell
+// can then be smaller than the float spacing at its position.
 __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ counts, const float4 *__restrict__ mom,
-                                                float inv_theta, float4 *mac, uint32_t *queue,
+                                                float inv_theta, float4 *mac, float4 *mac_lo, uint32_t *queue,
                                                 unsigned long long *pool_ctr, uint32_t *work_hist) {
   const int C = counts[0];
   if (blockIdx.x == 0) {  // the walk's group counters, list pool and cost histogram start empty
@@ -236,9 +270,10 @@ __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ coun
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     float4 a = mom[4 * (size_t)c];
-    float delta = mom[4 * (size_t)c + 1].w;
+    float4 b = mom[4 * (size_t)c + 1];
     float l = mom[4 * (size_t)c + 3].z;
-    mac[c] = make_float4(a.x, a.y, a.z, fmaf(l, inv_theta, delta));
+    mac[c] = make_float4(a.x, a.y, a.z, fmaf(l, inv_theta, b.w));
+    if (mac_lo) mac_lo[c] = make_float4(b.x, b.y, b.z, 0.f);
   }
 }
 
@@ -252,15 +287,15 @@ __global__ void __launch_bounds__(kBlock) k_clear_counters(const int32_t *__rest
 // The minimal-distance criterion's record: the cell's geometric centre
 // (rounded to float) and its half side l/2 (exact); the walk tests the gap
 // between this cube and the group's box against l/theta = (l/2)(2/theta).
-template <bool FOREST>
-__global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ counts,
-                                                    const uint64_t *__restrict__ skey,
+template <bool FOREST, bool DEEP>
+__global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ counts, const Keys K,
                                                     const int32_t *__restrict__ offs, int S,
                                                     const Frame *__restrict__ frame,
                                                     const FrameF *__restrict__ framef,
                                                     const int32_t *__restrict__ c_level,
-                                                    const int32_t *__restrict__ c_pbeg, float4 *mac, uint32_t *queue,
-                                                    unsigned long long *pool_ctr, uint32_t *work_hist) {
+                                                    const int32_t *__restrict__ c_pbeg, float4 *mac, float4 *mac_lo,
+                                                    uint32_t *queue, unsigned long long *pool_ctr,
+                                                    uint32_t *work_hist) {
   const int C = counts[0];
   if (blockIdx.x == 0) {  // the walk's group counters, list pool and cost histogram start empty
     if (threadIdx.x == 0) {
@@ -271,24 +306,35 @@ __global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ 
     for (int i = threadIdx.x; i < 2 * kCostBuckets; i += blockDim.x) work_hist[i] = 0;
   }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-    const Centre G = cell_centre<FOREST>(c_level[c] & 31, c_pbeg[c], skey, offs, S, frame, framef);
+    const Centre G = cell_centre<FOREST, DEEP>(c_level[c] & 31, c_pbeg[c], K, offs, S, frame, framef);
     mac[c] = make_float4(G.hi[0], G.hi[1], G.hi[2], 0.5f * G.l);
+    if (DEEP) mac_lo[c] = make_float4(G.lo[0], G.lo[1], G.lo[2], 0.f);
   }
 }
 
 }  // namespace
 
+template <bool FOREST, bool REFRESH, bool DEEP>
+static void moments_impl(Ctx &c, cudaStream_t s) {
+  const Keys K{c.key[0], c.skey_lo, c.levels};
+  k_moments<FOREST, REFRESH, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(
+      K, c.offs, c.n_sys, c.frame, c.framef, c.d_counts, c.c_level, c.c_pbeg, c.c_pend, c.c_parent, c.c_first,
+      c.c_nch, c.c_ctr, c.part_hi, c.part_lo, c.c_mom);
+}
+
 template <bool REFRESH>
 static void moments_launch(Ctx &c, cudaStream_t s) {
-  const int nb = c.num_sms * 8;
-  if (c.n_sys > 1)
-    k_moments<true, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.d_counts, c.c_level,
-                                                   c.c_pbeg, c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr,
-                                                   c.part_hi, c.part_lo, c.c_mom);
-  else
-    k_moments<false, REFRESH><<<nb, kBlock, 0, s>>>(c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.d_counts, c.c_level,
-                                                    c.c_pbeg, c.c_pend, c.c_parent, c.c_first, c.c_nch, c.c_ctr,
-                                                    c.part_hi, c.part_lo, c.c_mom);
+  const bool forest = c.n_sys > 1, deep = c.levels > kLevels;
+  if (forest) deep ? moments_impl<true, REFRESH, true>(c, s) : moments_impl<true, REFRESH, false>(c, s);
+  else deep ? moments_impl<false, REFRESH, true>(c, s) : moments_impl<false, REFRESH, false>(c, s);
+}
+
+template <bool FOREST, bool DEEP>
+static void mac_box_impl(Ctx &c, cudaStream_t s) {
+  const Keys K{c.key[0], c.skey_lo, c.levels};
+  k_mac_box<FOREST, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, K, c.offs, c.n_sys, c.frame, c.framef,
+                                                           c.c_level, c.c_pbeg, c.c_mac, c.c_mac_lo, c.walk_queue,
+                                                           c.pool_ctr, c.work_hist);
 }
 
 cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
@@ -310,14 +356,11 @@ cudaError_t launch_moments_refresh(Ctx &c, cudaStream_t s) {
 cudaError_t launch_mac(Ctx &c, float theta, cudaStream_t s) {
   float inv = (theta > 0.f) ? 1.0f / theta : INFINITY;
   if (c.p.mac == 1) {
-    if (c.n_sys > 1)
-      k_mac_box<true><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.c_level,
-                                                       c.c_pbeg, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
-    else
-      k_mac_box<false><<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.key[0], c.offs, c.n_sys, c.frame, c.framef, c.c_level,
-                                                        c.c_pbeg, c.c_mac, c.walk_queue, c.pool_ctr, c.work_hist);
+    const bool forest = c.n_sys > 1, deep = c.levels > kLevels;
+    if (forest) deep ? mac_box_impl<true, true>(c, s) : mac_box_impl<true, false>(c, s);
+    else deep ? mac_box_impl<false, true>(c, s) : mac_box_impl<false, false>(c, s);
   } else {
-    k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.walk_queue, c.pool_ctr,
+    k_mac<<<c.num_sms * 8, kBlock, 0, s>>>(c.d_counts, c.c_mom, inv, c.c_mac, c.c_mac_lo, c.walk_queue, c.pool_ctr,
                                            c.work_hist);
   }
   c.launches++;

@@ -142,17 +142,30 @@ __device__ __forceinline__ int cost_bucket(int w) {
   return 8 * msb + (int)frac;
 }
 
+// Offset of a two-float coordinate (h, l) from the float c: the difference of
+// the high parts (exact with its rounding error) plus the low part, rounded
+// once (hi) with the exact residual (lo).  The rounded offset is what the
+// opening test and the particle-cell terms read; it must be the correctly
+// rounded one, since the low part of a coordinate can exceed the size of the
+// smallest cells (keys deeper than 20 levels: cells of 6e-8 at 0.3, whose
+// float spacing is 3e-8).
+__device__ __forceinline__ void rounded_offset(float h, float l, float c, float &hi, float &lo) {
+  float e;
+  const float d = two_diff(h, c, e);  // d + e = h - c
+  const float r = e + l;              // |r| <= ulp(h): its rounding is below 2^-47 |h|
+  const float s = d + r;
+  const float bb = s - d;
+  lo = (d - (s - bb)) + (r - bb);  // TwoSum: s + lo = d + r
+  hi = s;
+}
+
 template <int VAR>
 __device__ __forceinline__ Target make_target(float4 h, float4 l, float cx, float cy, float cz) {
   Target t;
   if (VAR == 0) {
-    float ex, ey, ez;
-    t.hx = two_diff(h.x, cx, ex);
-    t.hy = two_diff(h.y, cy, ey);
-    t.hz = two_diff(h.z, cz, ez);
-    t.lx = ex + l.x;
-    t.ly = ey + l.y;
-    t.lz = ez + l.z;
+    rounded_offset(h.x, l.x, cx, t.hx, t.lx);
+    rounded_offset(h.y, l.y, cy, t.hy, t.ly);
+    rounded_offset(h.z, l.z, cz, t.hz, t.lz);
   } else {
     t.hx = h.x;
     t.hy = h.y;
@@ -167,6 +180,7 @@ struct TravArgs {
   const float4 *__restrict__ part_hi;
   const float4 *__restrict__ part_lo;
   const float4 *__restrict__ mac;
+  const float4 *__restrict__ mac_lo;  // keys deeper than 20 levels: the low parts of the records' positions
   const int2 *__restrict__ link;
   const int32_t *__restrict__ g_beg;
   const int32_t *__restrict__ g_sys;
@@ -262,7 +276,7 @@ __device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int l
     int *cstk = cur, *nstk = nxt;
     int depth = 0;
     while (ncur > 0) {
-      if (++depth > kLevels + 1) {  // a tree has at most 21 levels: never loop on a corrupt one
+      if (++depth > kLevelsMax + 1) {  // a tree has at most D + 1 <= 31 levels: never loop on a corrupt one
         if (lane == 0) set_status(A.status, BH_ERR_STATE);
         break;
       }
@@ -289,7 +303,13 @@ __device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int l
           lk_n = A.link[ci_n];
         }
         if (base + 64 + lane < ncur) ci_nn = cstk[base + 64 + lane];
-        const float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
+        float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
+        if (A.mac_lo && have) {  // cells below level 20 can be smaller than the float spacing at their position
+          const float4 ml = A.mac_lo[ci];
+          rx += ml.x;
+          ry += ml.y;
+          rz += ml.z;
+        }
         float ex, ey, ez, ro;
         if (!A.box_mac) {  // Eq. 1: the centre of mass's distance to the box against r_open = m.w
           ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
@@ -1073,6 +1093,7 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   t.part_hi = c.part_hi;
   t.part_lo = c.part_lo;
   t.mac = c.c_mac;
+  t.mac_lo = c.c_mac_lo;
   t.link = c.c_link;
   t.g_beg = c.g_beg;
   t.g_sys = c.g_sys;
