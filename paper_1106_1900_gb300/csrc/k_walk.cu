@@ -39,11 +39,15 @@
 // small enough for three or four slots per body (eval_passes).
 //
 // Precision (variant 0): coordinates are offsets from the group centre c (a
-// float: the first body's position), each kept as two floats -- the rounded
-// offset and its exact residual -- built from the two-float body positions.
-// Particle-particle terms difference both parts, so a close pair stays
-// accurate however far from c it lies; particle-cell terms use the rounded
-// part (accepted cells lie at least l/theta from the group's box).  Partial
+// float: the first body's position), each kept as two floats -- the
+// difference of the high parts and the rest, hi + lo the offset to ~2^-48 --
+// built from the two-float body positions.  Particle-particle terms
+// difference both parts, so a close pair stays accurate however far from c it
+// lies; particle-cell terms use the high part, which is off by at most the
+// body's low part (2^-25 of its coordinate), far below l/theta for any cell
+// of a 20-level tree.  Keys deeper than 20 levels take variant 3: the high
+// part is the correctly rounded offset and the opening test also reads the
+// low part of each cell's position (a level-30 cell is 2^-30 L).  Partial
 // sums (about 32 interactions per slot) are folded into a (hi, lo) pair by
 // TwoSum.  Variant 1 is the naive form: absolute FP32 coordinates and plain
 // sums.  A body is never paired with itself: particle tiles that hold bodies
@@ -67,6 +71,14 @@ constexpr int kWalkMinBlocks = 6;  // the fused walk (7 measured slower at N_cri
 // k ceil(32 / k) - 1, and k = 32 / h is one of 1, 2, 3, 4, 5, 6, 8, 10, 16,
 // 32: at most entry 39 (k = 10).
 constexpr int kStage = 40;
+
+// Arithmetic variants: 0 group-relative FP32 with compensated tiles, 1 naive
+// FP32; 3 is variant 0 for keys deeper than 20 levels, whose cells can be
+// smaller than the float spacing at their position: offsets from the group
+// centre are rounded once from the whole two-float difference, and the
+// opening test adds the low part of each record's position.
+constexpr int kVarDeep = 3;
+__host__ __device__ constexpr bool relative(int var) { return var == 0 || var == kVarDeep; }
 
 struct Target {
   float hx, hy, hz;  // offset from the group centre, rounded
@@ -162,10 +174,18 @@ __device__ __forceinline__ void rounded_offset(float h, float l, float c, float 
 template <int VAR>
 __device__ __forceinline__ Target make_target(float4 h, float4 l, float cx, float cy, float cz) {
   Target t;
-  if (VAR == 0) {
+  if (VAR == kVarDeep) {
     rounded_offset(h.x, l.x, cx, t.hx, t.lx);
     rounded_offset(h.y, l.y, cy, t.hy, t.ly);
     rounded_offset(h.z, l.z, cz, t.hz, t.lz);
+  } else if (VAR == 0) {  // the difference of the high parts and the rest: enough where cells exceed 2^-20 L
+    float ex, ey, ez;
+    t.hx = two_diff(h.x, cx, ex);
+    t.hy = two_diff(h.y, cy, ey);
+    t.hz = two_diff(h.z, cz, ez);
+    t.lx = ex + l.x;
+    t.ly = ey + l.y;
+    t.lz = ez + l.z;
   } else {
     t.hx = h.x;
     t.hy = h.y;
@@ -242,7 +262,7 @@ __device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int l
     const int n = A.g_beg[g + 1] - gb;
     // group centre and tight bounding box (offsets from the centre, rounded)
     float cx = 0.f, cy = 0.f, cz = 0.f;
-    if (VAR == 0) {
+    if (relative(VAR)) {
       const float4 c = A.part_hi[gb];
       cx = c.x;
       cy = c.y;
@@ -304,7 +324,7 @@ __device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int l
         }
         if (base + 64 + lane < ncur) ci_nn = cstk[base + 64 + lane];
         float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
-        if (A.mac_lo && have) {  // cells below level 20 can be smaller than the float spacing at their position
+        if (VAR == kVarDeep && have) {  // cells below level 20 can be smaller than the float spacing at their position
           const float4 ml = A.mac_lo[ci];
           rx += ml.x;
           ry += ml.y;
@@ -587,7 +607,7 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 template <int VAR>
 __device__ __forceinline__ void fold(float4 &hs, float4 &ls, float x, float y, float z, float p) {
   float4 hi = hs, lo = ls;
-  if (VAR == 0) {
+  if (relative(VAR)) {
     two_sum_into(hi.x, lo.x, x);
     two_sum_into(hi.y, lo.y, y);
     two_sum_into(hi.z, lo.z, z);
@@ -620,7 +640,7 @@ template <int VAR, bool GUARD, bool SELF>
 __device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 sh, const float4 sl, float2 e2,
                                     int me0 = 0, int me1 = 0, int other = -1) {
   float2 dx, dy, dz;
-  if (VAR == 0) {
+  if (relative(VAR)) {
     dx = __fadd2_rn(__fadd2_rn(f2(sh.x, sh.x), t.nhx), __fadd2_rn(f2(sl.x, sl.x), t.nlx));
     dy = __fadd2_rn(__fadd2_rn(f2(sh.y, sh.y), t.nhy), __fadd2_rn(f2(sl.y, sl.y), t.nly));
     dz = __fadd2_rn(__fadd2_rn(f2(sh.z, sh.z), t.nhz), __fadd2_rn(f2(sl.z, sl.z), t.nlz));
@@ -707,7 +727,7 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
   const int gb0 = A.g_beg[g];
   const int ng = A.g_beg[g + 1] - gb0;
   float cx = 0.f, cy = 0.f, cz = 0.f;
-  if (VAR == 0) {
+  if (relative(VAR)) {
     const float4 c = A.part_hi[gb0];
     cx = c.x;
     cy = c.y;
@@ -762,7 +782,7 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
         const int cnt = min(32, nc - base);
         if (lane < cnt) {
           float dx, dy, dz;
-          if (VAR == 0) {
+          if (relative(VAR)) {
             dx = (ra.x - cx) + rb.x;
             dy = (ra.y - cy) + rb.y;
             dz = (ra.z - cz) + rb.z;
@@ -1064,6 +1084,10 @@ cudaError_t walk_init_attrs(int smem) {
   BH_EVAL_ATTR(1, true, kOutCaller)
   BH_EVAL_ATTR(1, false, kOutSorted)
   BH_EVAL_ATTR(1, true, kOutSorted)
+  BH_EVAL_ATTR(kVarDeep, false, kOutCaller)
+  BH_EVAL_ATTR(kVarDeep, true, kOutCaller)
+  BH_EVAL_ATTR(kVarDeep, false, kOutSorted)
+  BH_EVAL_ATTR(kVarDeep, true, kOutSorted)
 #undef BH_EVAL_ATTR
   return e;
 }
@@ -1133,7 +1157,9 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   a.acc_out = acc;
   a.pot_out = pot;
   a.perm = c.idx[0];
-  const int var = c.p.walk_variant;
+  // keys deeper than 20 levels take the deep form of variant 0 (and of the FP64 variant's walk)
+  const bool deep = c.levels > kLevels;
+  const int var = (c.p.walk_variant == 0 && deep) ? kVarDeep : c.p.walk_variant;
   const bool guard = !(a.eps2 > 0.f);
   const bool fused = walk_is_fused(c.p) || g_active;  // a walk of some groups only is always fused
   cudaError_t e = cudaSuccess;
@@ -1165,6 +1191,10 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
     BH_WALK_CASE(1, true, kOutCaller)
     BH_WALK_CASE(1, false, kOutSorted)
     BH_WALK_CASE(1, true, kOutSorted)
+    BH_WALK_CASE(kVarDeep, false, kOutCaller)
+    BH_WALK_CASE(kVarDeep, true, kOutCaller)
+    BH_WALK_CASE(kVarDeep, false, kOutSorted)
+    BH_WALK_CASE(kVarDeep, true, kOutSorted)
     e = cudaErrorInvalidValue;
 #undef BH_WALK_CASE
     mark(1);
@@ -1172,6 +1202,7 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
     return e;
   }
   if (var == 1) k_traverse<1><<<c.trav_grid, kThreads, 0, s>>>(t);
+  else if (deep) k_traverse<kVarDeep><<<c.trav_grid, kThreads, 0, s>>>(t);
   else k_traverse<0><<<c.trav_grid, kThreads, 0, s>>>(t);
   e = cudaGetLastError();
   c.launches++;
@@ -1197,6 +1228,10 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   BH_EVAL_CASE(1, true, kOutCaller)
   BH_EVAL_CASE(1, false, kOutSorted)
   BH_EVAL_CASE(1, true, kOutSorted)
+  BH_EVAL_CASE(kVarDeep, false, kOutCaller)
+  BH_EVAL_CASE(kVarDeep, true, kOutCaller)
+  BH_EVAL_CASE(kVarDeep, false, kOutSorted)
+  BH_EVAL_CASE(kVarDeep, true, kOutSorted)
   e = cudaErrorInvalidValue;
 #undef BH_EVAL_CASE
   mark(1);

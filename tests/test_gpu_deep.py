@@ -39,31 +39,23 @@ def test_deep_keys_nested_cluster(cuda_lib, D):
 
 def test_deep_keys_equal_20_levels_when_uncrowded(cuda_lib):
     # no level-20 cell holds more than N_leaf bodies: the same tree and moments
-    # bit for bit; the opening test of deeper keys also reads the low part of
-    # each record's position, so a decision at a float-rounding tie may differ
+    # bit for bit; the walks differ in rounding (30-level keys round each
+    # offset once, and also read the low part of each cell position in the
+    # opening test), so both are held to the oracle's forces
     pos, _, m = ics.plummer(16384, 1)
+    acc_o, pot_o, t, st_o = oracle.tree_forces(pos, m, 0.5, 0.01, 16, 64)
     out = []
     for D in (20, 30):
         tc, acc, pot = _run(cuda_lib, pos, m, 0.5, 0.01, 16, 64, key_levels=D)
-        out.append((tc.tree(), tc.moments(), tc.group_stats(), acc, pot))
-    (ta, ma, ga, aa, pa), (tb, mb, gb, ab, pb) = out
+        out.append((tc.tree(), tc.moments()))
+        P.compare_forces(acc, pot, acc_o, pot_o, t, st_o, tc.group_stats())
+    (ta, ma), (tb, mb) = out
     for k in ("skey", "perm", "level", "pbeg", "pend", "parent", "first_child", "n_children", "is_leaf", "gbeg",
               "gend"):
         assert np.array_equal(ta[k], tb[k]), k
     assert ta["level"].max() < 20 and tb["skey_lo"].any()  # low words exist but split no cell
     for k in ma:
         assert np.array_equal(ma[k], mb[k]), k
-    same = np.ones(len(ga["nc"]), bool)
-    for k in ga:
-        same &= ga[k] == gb[k]
-    assert same.mean() > 0.99
-    gs = P.group_of_sorted(ta["gbeg"], len(pos))
-    g_in = np.empty(len(pos), dtype=np.int64)
-    g_in[ta["perm"]] = gs
-    eq = same[g_in]
-    assert np.array_equal(aa[eq], ab[eq]) and np.array_equal(pa[eq], pb[eq])
-    an = np.linalg.norm(aa, axis=1)
-    assert np.all(np.linalg.norm(aa - ab, axis=1) <= P.FLIP_TOL * an)
 
 
 def test_deep_keys_forest(cuda_lib):
