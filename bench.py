@@ -218,11 +218,13 @@ def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
                       f"theta={theta}, eps={eps}"}
 
 
-def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.05):
+def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.05,
+                  rebuild_every=False):
     """Block time-steps on the same workload: one synchronised interval of
-    dt_max (rebuild at its start, moment refresh inside it), against stepping
-    every body with the smallest step any body used in it (what a shared step
-    needs for the same per-body accuracy), timed by one shared step."""
+    dt_max (a rebuild at every block step, or at the interval's start with
+    moment refreshes inside it), against stepping every body with the
+    smallest step any body used in it (what a shared step needs for the same
+    per-body accuracy), timed by one shared step."""
     import torch
 
     n = pos.shape[0]
@@ -239,7 +241,7 @@ def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, 
         deepest = 0
         tick = t0
         while tick < t0 + sync:
-            rebuild = tick % sync == 0
+            rebuild = rebuild_every or tick % sync == 0
             tc.block_step(theta, eps, rebuild=rebuild)
             info = tc.block_info()  # (the one host synchronisation of a block step)
             tick = info["tick"]
@@ -264,9 +266,10 @@ def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, 
     torch.cuda.synchronize()
     shared_ms = a.elapsed_time(b) / 5
     shared_interval_s = shared_ms * 1e-3 * 2 ** deepest
+    policy = "a rebuild at every block step" if rebuild_every else "rebuild at its start, moment refresh inside"
     return {"what": f"block time-steps, dt_max = 1/{round(1 / dt_max)}, k_max = {k_max}, eta = {eta}: one "
-                    "synchronised dt_max interval (host-driven block steps, rebuild at its start, moment refresh "
-                    "inside) against shared steps of the smallest step used",
+                    f"synchronised dt_max interval (host-driven block steps, {policy}) against shared steps of "
+                    "the smallest step used",
             "block_steps": steps, "rebuilds": rebuilds, "deepest_level": deepest,
             "body_updates": updates, "updates_per_s": updates / wall, "interval_s": wall,
             "shared_step_ms": shared_ms, "shared_interval_s": shared_interval_s,
@@ -520,7 +523,9 @@ def main():
         ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=3, warmup=2)
     blk = None
     if args.block:
-        blk = block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta)
+        blk = {"rebuild_every_step": block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta,
+                                                   rebuild_every=True),
+               "refresh_inside": block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(pos, m, args.theta, eps)
