@@ -215,6 +215,14 @@ int bh_status(bh_ctx *ctx, void *stream);
  * by the library since reset. */
 int bh_get_counts(bh_ctx *ctx, int64_t out[9], void *stream);
 
+/* Failure detection test hook: runs the sort's bounded look-back wait on a
+ * tile table that nothing publishes, so it gives up after spin_limit polls
+ * (>= 1, capped at the library's own limit of 2^22) and latches
+ * BH_ERR_TIMEOUT in the status word, which bh_status then returns (and
+ * clears); the context stays usable.  Overwrites the sort's scratch and drops
+ * captured step graphs.  BH_ERR_INVALID_ARG for spin_limit < 1. */
+int bh_wait_probe(bh_ctx *ctx, int32_t spin_limit, void *stream);
+
 /* Clears the interaction and launch counters of bh_get_counts. */
 int bh_reset_counters(bh_ctx *ctx, void *stream);
 

@@ -138,6 +138,7 @@ _SIG = {
     "bh_reset_counters": [ctypes.c_void_p, ctypes.c_void_p],
     "bh_get_tree": [ctypes.c_void_p] + [ctypes.c_void_p] * 11 + [ctypes.c_void_p],
     "bh_get_keys_lo": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "bh_wait_probe": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p],
     "bh_get_moments": [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_void_p],
     "bh_get_group_stats": [ctypes.c_void_p] + [ctypes.c_void_p] * 4 + [ctypes.c_void_p],
     "bh_set_profiling": [ctypes.c_void_p, ctypes.c_int],
@@ -361,6 +362,11 @@ class TreeCode:
 
     def check(self, stream=None):
         _check(self.status(stream), "device status")
+
+    def wait_probe(self, spin_limit: int = 1000, stream=None):
+        """Run a bounded device wait that nothing ends (failure-detection test
+        hook); the status word then reads BH_ERR_TIMEOUT."""
+        _check(self.lib.bh_wait_probe(self.ctx, spin_limit, _stream(stream)), "bh_wait_probe")
 
     def counts(self, stream=None) -> dict:
         out = (ctypes.c_int64 * 9)()

@@ -755,6 +755,16 @@ int bh_status(bh_ctx *ctx, void *stream) {
   return st;
 }
 
+int bh_wait_probe(bh_ctx *ctx, int32_t spin_limit, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  if (spin_limit < 1) return BH_ERR_INVALID_ARG;
+  Ctx &c = ctx->c;
+  DeviceGuard g(c.device);
+  drop_graphs(c);  // the probe reuses the sort's tile table
+  return cu(bh::launch_wait_probe(c, spin_limit, (cudaStream_t)stream));
+}
+
 int bh_get_counts(bh_ctx *ctx, int64_t out[9], void *stream) {
   int rc = ready(ctx);
   if (rc) return rc;

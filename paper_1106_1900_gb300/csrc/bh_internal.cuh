@@ -149,6 +149,7 @@ cudaError_t launch_reset(Ctx &c, cudaStream_t s);
 cudaError_t launch_frame_keys(Ctx &c, const double *pos, const double *mass, cudaStream_t s);
 cudaError_t launch_sort(Ctx &c, cudaStream_t s);  // key[0]/idx[0] -> sorted key[0]/idx[0]
 cudaError_t launch_move(Ctx &c, const double *pos, const double *mass, cudaStream_t s);
+cudaError_t launch_wait_probe(Ctx &c, int limit, cudaStream_t s);  // failure path of a bounded wait
 cudaError_t launch_move_state(Ctx &c, cudaStream_t s);  // gather state cur -> other, fills part_hi/lo
 cudaError_t launch_cells(Ctx &c, cudaStream_t s);
 cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);

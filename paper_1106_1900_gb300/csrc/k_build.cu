@@ -443,6 +443,28 @@ __global__ void __launch_bounds__(kBlock) k_gather_key(const uint32_t *__restric
   if (j < n) dst[j] = src[idx[j]];
 }
 
+// The failure path of the sort's look-back, run on purpose: each thread polls
+// kLookback status words of a tile table that nothing publishes, the way a
+// tile polls its predecessors, and gives up after `limit` polls without
+// progress, latching BH_ERR_TIMEOUT (the context stays usable).
+__global__ void __launch_bounds__(kBlock) k_wait_probe(const uint32_t *status, int limit, int32_t *err) {
+  const int t = threadIdx.x;
+  int spins = 0;
+  while (true) {
+    uint32_t w[kLookback];
+#pragma unroll
+    for (int q = 0; q < kLookback; ++q) w[q] = __ldcv(&status[(size_t)q * 256 + t]);
+    int q = 0;
+    while (q < kLookback && (w[q] & ~kValMask) != 0) ++q;
+    if (q == kLookback) return;  // (never: nothing publishes)
+    if (++spins > limit) {
+      set_status(err, BH_ERR_TIMEOUT);
+      return;
+    }
+    __nanosleep(32);
+  }
+}
+
 // ----------------------------------------------------------------- move
 __global__ void __launch_bounds__(kBlock) k_move(const double *__restrict__ pos, const double *__restrict__ mass,
                                                  const uint32_t *__restrict__ perm, int n, float4 *part_hi,
@@ -917,6 +939,15 @@ cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
     k_gather_key<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.idx[0], c.key_lo0, c.skey_lo, n);
     c.launches++;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_probe(Ctx &c, int limit, cudaStream_t s) {
+  // a tile table of kLookback tiles, all unpublished
+  cudaError_t e = cudaMemsetAsync(c.sort_status, 0, sizeof(uint32_t) * kLookback * 256, s);
+  if (e) return e;
+  k_wait_probe<<<1, kBlock, 0, s>>>(c.sort_status, limit < 1 ? 1 : min(limit, kSpinLimit), c.d_status);
+  c.launches++;
   return cudaGetLastError();
 }
 

@@ -164,6 +164,27 @@ def test_stack_overflow_is_reported(cuda_lib):
     assert tc.status() == 0  # the status word was cleared
 
 
+def test_bounded_wait_gives_up(cuda_lib):
+    # a look-back wait on tiles that nothing publishes gives up, latches the
+    # timeout and leaves the context usable
+    import torch
+
+    pos, _, m = ics.plummer(4000, 6)
+    tc = cuda_lib.TreeCode(4000)
+    tc.wait_probe(1000)
+    assert tc.status() == 4  # BH_ERR_TIMEOUT
+    assert tc.status() == 0  # the status word was cleared
+    tc.build(_dev(pos), _dev(m))
+    acc = torch.empty((4000, 3), dtype=torch.float32, device="cuda")
+    pot = torch.empty(4000, dtype=torch.float32, device="cuda")
+    tc.compute_forces(0.5, 0.01, acc, pot)
+    tc.check()
+    acc_o, _, _, _ = oracle.tree_forces(pos, m, 0.5, 0.01)
+    assert np.allclose(acc.cpu().numpy(), acc_o, rtol=1e-3, atol=1e-3 * np.abs(acc_o).max())
+    with pytest.raises(Exception):
+        tc.wait_probe(0)
+
+
 # ----------------------------------------------------------------- forest
 def test_forest_parity(cuda_lib):
     pos, _, m, off = ics.ensemble(n_sys=40, seed=9, n_min=1, n_max=3000)
