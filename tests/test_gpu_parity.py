@@ -53,12 +53,20 @@ def _full_parity(bh, pos, mass, theta, eps, n_leaf=16, n_crit=64, offsets=None, 
 def test_scan_worked_example(cuda_lib):
     import torch
 
+    import os
+
+    g = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "scan_example.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split(None, 1)
+                g[k] = [int(w) for w in v.split()]
     tc = cuda_lib.TreeCode(1 << 16)
-    x = torch.tensor([3, 1, 7, 0, 4, 1, 6, 3], dtype=torch.int32, device="cuda")
+    x = torch.tensor(g["input"], dtype=torch.int32, device="cuda")
     ex, total = tc.exclusive_scan(x)
     inclusive = (ex + x).cpu().numpy().tolist()
-    assert inclusive == [3, 4, 11, 11, 15, 16, 22, 25]
-    assert total == 25
+    assert inclusive == g["output"]
+    assert total == g["output"][-1]
 
 
 @pytest.mark.parametrize("n", [1, 4095, 4096, 4097, 60001])
