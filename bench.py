@@ -188,15 +188,15 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
-    the whole tree build plus the walk of every k-th group."""
+def cpu_baseline(pos, mass, theta, eps, n_leaf=16, n_crit=64, target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload
+    (same N_leaf, N_crit): the whole tree build plus the walk of every k-th group."""
     import numpy as np
 
     import oracle
 
     t0 = time.perf_counter()
-    t = oracle.build_tree(pos, mass)
+    t = oracle.build_tree(pos, mass, n_leaf, n_crit)
     t_build = time.perf_counter() - t0
     # size the sample from a short probe so that the walk takes ~target_s
     probe = np.arange(0, t.G, max(1, t.G // 64))
@@ -215,7 +215,7 @@ def cpu_baseline(pos, mass, theta, eps, target_s=15.0):
     return {"value": bodies / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 tree build of all {t.n} bodies ({t_build:.2f} s, charged pro rata) + walk of "
                       f"every {k}-th group ({len(groups)} groups, {bodies} bodies, {t_walk:.2f} s), "
-                      f"theta={theta}, eps={eps}"}
+                      f"theta={theta}, eps={eps}, N_leaf={n_leaf}, N_crit={n_crit}"}
 
 
 def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.05,
@@ -353,8 +353,12 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     pos, vel, m = ics.plummer(args.n, SEED)
+    from paper_1106_1900_gb300 import autotune  # (the cached parameters only: no GPU, no library)
+
+    tuned = None if args.untuned else autotune.tuned_params(args.n, args.theta, "plummer")
+    nl, nc = (tuned["n_leaf"], tuned["n_crit"]) if tuned else (16, 64)
     t0 = time.perf_counter()
-    t = oracle.build_tree(pos, m)
+    t = oracle.build_tree(pos, m, nl, nc)
     t_build = time.perf_counter() - t0
     budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
     probe = np.arange(0, t.G, max(1, t.G // 32))
@@ -367,7 +371,7 @@ def run_reference(args):
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        tt = oracle.build_tree(pos, m)
+        tt = oracle.build_tree(pos, m, nl, nc)
         tb = time.perf_counter() - t0
         t0 = time.perf_counter()
         oracle.walk(tt, args.theta, EPS, groups)
@@ -378,13 +382,13 @@ def run_reference(args):
     value = bodies * len(times) / secs
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     sample = (f"per step: FP64 tree build of all {args.n} bodies (charged pro rata) + walk of every {k}-th "
-              f"group ({len(groups)} groups, {bodies} bodies)")
+              f"group ({len(groups)} groups, {bodies} bodies), N_leaf={nl}, N_crit={nc}")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times) * args.n / bodies,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"Plummer N={args.n}, theta={args.theta}, eps={EPS}, seed={SEED}",
-                   "global_batch": args.n, "parallelism": "oracle on host cores"},
+                   "global_batch": args.n, "parallelism": "oracle on host cores", "n_leaf": nl, "n_crit": nc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -528,7 +532,7 @@ def main():
                "refresh_inside": block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pos, m, args.theta, eps)
+        cpu = cpu_baseline(pos, m, args.theta, eps, tc.params.n_leaf, tc.params.n_crit)
     if rank != 0:
         return
     cnt = tc.counts()
