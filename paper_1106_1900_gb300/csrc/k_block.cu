@@ -18,6 +18,8 @@
 //                    when T is a multiple of the doubled step)
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "bh_internal.cuh"
 
 namespace bh {
@@ -30,29 +32,33 @@ inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 __device__ __forceinline__ long long step_ticks(int kmax, int k) { return 1ll << (kmax - k); }
 
 // The level a body with acceleration a wants: the smallest k >= 0 with
-// dt_max 2^-k <= eta sqrt(eps / |a|), i.e. 2^k >= r = dt_max sqrt(|a| / eps) / eta
-// (FP64 from the FP32 components), clamped to kmax.
-__device__ __forceinline__ int wanted_level(float4 a, double dt_max, double eps, double eta, int kmax) {
-  const double ax = a.x, ay = a.y, az = a.z;
-  const double am = sqrt(ax * ax + ay * ay + az * az);
-  const double r = dt_max * sqrt(am / eps) / eta;
-  if (!(r > 1.0)) return 0;
-  int e = 0;
-  const double m = frexp(r, &e);  // r = m 2^e, m in [0.5, 1)
-  const int k = (m == 0.5) ? e - 1 : e;
+// dt_max 2^-k <= eta sqrt(eps / |a|), i.e. 2^k >= r = c |a|^(1/2) with
+// c = dt_max / (eta sqrt(eps)) (from the host, FP64 rounded to float); in
+// FP32, as the accelerations are, with k read from r's exponent bits (r is
+// then a normal float above 1); clamped to kmax.  NaN gives 0.
+__device__ __forceinline__ int wanted_level(float4 a, float c, int kmax) {
+  const float s = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+  const float r = c * sqrtf(sqrtf(s));
+  if (!(r > 1.f)) return 0;
+  const unsigned b = __float_as_uint(r);
+  const int e = (int)((b >> 23) & 0xffu) - 127;  // r = 1.f 2^e
+  const int k = (b & 0x7fffffu) ? e + 1 : e;     // a power of two needs no more
   return min(k, kmax);
 }
 
 __global__ void __launch_bounds__(kBlock) k_block_levels(int n, const float4 *__restrict__ a, int64_t *t, int32_t *k,
-                                                         double dt_max, double eps, double eta, int kmax,
-                                                         unsigned long long *blk) {
+                                                         float c_level, int kmax, unsigned long long *blk) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) blk[0] = 0;
-  if (i >= n) return;
-  t[i] = 0;
-  const int lv = wanted_level(a[i], dt_max, eps, eta, kmax);
-  k[i] = lv;
-  atomicMax(&blk[2], (unsigned long long)lv);
+  unsigned lv = 0;
+  if (i < n) {
+    t[i] = 0;
+    lv = (unsigned)wanted_level(a[i], c_level, kmax);
+    k[i] = (int32_t)lv;
+  }
+  // deepest level: one atomic per warp (one per body serialises on one address)
+  lv = __reduce_max_sync(kFull, lv);
+  if ((threadIdx.x & 31) == 0) atomicMax(&blk[2], (unsigned long long)lv);
 }
 
 // blk[0] = min over bodies of the next due time (blk[0] preset to all ones)
@@ -150,16 +156,12 @@ __global__ void __launch_bounds__(kBlock) k_group_active(const int32_t *__restri
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_block_correct(int n, double *x, double *v, float4 *a_old,
-                                                          int64_t *t, int32_t *k, const float4 *__restrict__ a_new,
-                                                          const double *__restrict__ pred, int kmax, double tick,
-                                                          double dt_max, double eps, double eta,
-                                                          unsigned long long *blk) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const long long T = (long long)blk[0];
-  const long long s = step_ticks(kmax, k[i]);
-  if (t[i] + s != T) return;
+// One due body: the leapfrog corrector of k_correct, then the level rule;
+// returns the new level.
+__device__ __forceinline__ unsigned correct_body(int i, long long s, long long T, double *x, double *v,
+                                                 float4 *a_old, int64_t *t, int32_t *k,
+                                                 const float4 *__restrict__ a_new, const double *__restrict__ pred,
+                                                 int kmax, double tick, float c_level) {
   const double dt = (double)s * tick;
   const float4 o = a_old[i], w = a_new[i];
   const double h = 0.5 * dt;
@@ -174,12 +176,26 @@ __global__ void __launch_bounds__(kBlock) k_block_correct(int n, double *x, doub
   a_old[i] = w;
   t[i] = T;
   // level rule: deeper at once; one level shallower when T is a multiple of the doubled step
-  const int want = wanted_level(w, dt_max, eps, eta, kmax);
+  const int want = wanted_level(w, c_level, kmax);
   int kn = k[i];
   if (want > kn) kn = want;
   else if (want < kn && kn > 0 && T % (2 * s) == 0) kn = kn - 1;
   k[i] = kn;
-  atomicMax(&blk[2], (unsigned long long)kn);
+  return (unsigned)kn;
+}
+
+__global__ void __launch_bounds__(kBlock) k_block_correct(int n, double *x, double *v, float4 *a_old,
+                                                          int64_t *t, int32_t *k, const float4 *__restrict__ a_new,
+                                                          const double *__restrict__ pred, int kmax, double tick,
+                                                          float c_level, unsigned long long *blk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long T = (long long)blk[0];
+  const long long s = (i < n) ? step_ticks(kmax, k[i]) : 0;
+  const bool act = i < n && t[i] + s == T;
+  const unsigned kn = act ? correct_body(i, s, T, x, v, a_old, t, k, a_new, pred, kmax, tick, c_level) : 0u;
+  // deepest level: one atomic per warp (one per body serialises on one address)
+  const unsigned km = __reduce_max_sync(kFull, kn);
+  if ((threadIdx.x & 31) == 0 && __any_sync(kFull, act)) atomicMax(&blk[2], (unsigned long long)km);
 }
 
 // levels and ticks in the caller's order
@@ -195,6 +211,9 @@ __global__ void __launch_bounds__(kBlock) k_block_get(int n, const int32_t *__re
 
 }  // namespace
 
+// c = dt_max / (eta sqrt(eps)) of the level rule
+static float level_factor(const Ctx &c, double eps) { return (float)(c.blk_dt_max / (c.blk_eta * std::sqrt(eps))); }
+
 cudaError_t launch_block_get(Ctx &c, int32_t *level, int64_t *tick, cudaStream_t s) {
   const int a = c.state_cur;
   k_block_get<<<cdiv(c.n, kBlock), kBlock, 0, s>>>((int)c.n, c.st_id[a], c.st_k[a], c.st_t[a], level, tick);
@@ -206,8 +225,8 @@ cudaError_t launch_block_levels(Ctx &c, double eps, cudaStream_t s) {
   const int a = c.state_cur;
   cudaError_t e = cudaMemsetAsync(c.d_block, 0, 4 * sizeof(unsigned long long), s);
   if (e) return e;
-  k_block_levels<<<cdiv(c.n, kBlock), kBlock, 0, s>>>((int)c.n, c.st_a[a], c.st_t[a], c.st_k[a], c.blk_dt_max, eps,
-                                                      c.blk_eta, c.blk_kmax, c.d_block);
+  k_block_levels<<<cdiv(c.n, kBlock), kBlock, 0, s>>>((int)c.n, c.st_a[a], c.st_t[a], c.st_k[a],
+                                                      level_factor(c, eps), c.blk_kmax, c.d_block);
   c.launches++;
   return cudaGetLastError();
 }
@@ -254,8 +273,7 @@ cudaError_t launch_block_correct(Ctx &c, double eps, bool rebuilt, cudaStream_t 
   const int a = c.state_cur;
   k_block_correct<<<cdiv(c.n, kBlock), kBlock, 0, s>>>((int)c.n, c.st_x[a], c.st_v[a], c.st_a[a], c.st_t[a],
                                                        c.st_k[a], c.acc_sorted, rebuilt ? c.pred_s : c.pred_x,
-                                                       c.blk_kmax, c.blk_tick, c.blk_dt_max, eps, c.blk_eta,
-                                                       c.d_block);
+                                                       c.blk_kmax, c.blk_tick, level_factor(c, eps), c.d_block);
   c.launches++;
   return cudaGetLastError();
 }

@@ -1,11 +1,21 @@
 // k_walk.cu -- the breadth-first group walk and force evaluation (§2.2, §3.3).
 //
 // The paper walks and evaluates in one kernel: a group's interaction lists
-// fill shared memory and are evaluated whenever a tile is full.  On a GB300
-// the two halves want different machines: the walk is a chain of dependent
-// L2 reads (it wants many resident warps and few registers), the evaluation
-// is FP32 arithmetic (it wants registers for its targets and accumulators and
-// a prefetched next tile).  So they are two persistent kernels here:
+// fill shared memory and are evaluated whenever a tile is full.  Here one
+// warp does a group at a time, in two halves: traverse_group walks the tree
+// and writes the group's two lists to the warp's own scratch (global memory,
+// L2-resident), then eval_group sums them tile by tile.  The default kernel
+// runs both halves per group:
+//
+//  k_size_hist, k_order   place the groups by size, largest first (the cost
+//              of a group is not known before its walk).
+//  k_walk      persistent warps take groups from a counter in that order,
+//              walk each and evaluate its lists straight from the scratch:
+//              no list pool, and other warps' arithmetic runs while a warp
+//              walks.
+//
+// The split form (walk_split = 1; the FP64 evaluation variant always) runs
+// the halves as separate persistent kernels, bit-identical in result:
 //
 //  k_traverse  one warp per group (groups taken from a counter).  The current
 //              level of the walk is read 32 cells at a time from a per-warp
