@@ -359,21 +359,21 @@ def _sampled_parity(bh, pos, m, theta, eps, every, offsets=None, **kw):
 
 
 def test_plummer_1m_sampled(cuda_lib):
-    """The benchmark's workload (configs[1]): 2^20-body Plummer sphere, theta = 0.5."""
+    """The benchmark's workload: 2^20-body Plummer sphere, theta = 0.5, eps = 0.005."""
     pos, _, m = ics.plummer(1 << 20, 2)
     _sampled_parity(cuda_lib, pos, m, 0.5, 0.005, every=400)
 
 
 def test_galaxy_8m_sampled(cuda_lib):
-    """Hernquist sphere + exponential disk, 8,388,608 bodies (configs[2]): a sparse,
-    very non-uniform tree."""
+    """Hernquist sphere + exponential disk, 8,388,608 bodies: a sparse, very
+    non-uniform tree."""
     pos, _, m = ics.galaxy(4194304, 4194304, 3)
     t, flipped = _sampled_parity(cuda_lib, pos, m, 0.5, 0.01, every=3000, pool_per_body=512)
     assert np.bincount(t.level).size > 12  # a deep tree
 
 
 def test_ensemble_7m_sampled(cuda_lib):
-    """512 Plummer clusters, ~7.7M bodies in one forest (configs[4])."""
+    """512 Plummer clusters of 1,024..65,536 bodies, ~7.7M bodies in one forest."""
     pos, _, m, off = ics.ensemble(512, 5)
     t, flipped = _sampled_parity(cuda_lib, pos, m, 0.5, 0.01, every=3000, offsets=off, pool_per_body=512)
     assert t.sys_root.min() >= 0
