@@ -160,3 +160,34 @@ def test_block_energy_over_synchronised_intervals(cuda_lib):
     assert abs((e1 - e0) / e0) < 2e-4
     assert updates < n * 8 * 2 ** tc.block_info()["deepest"]
     assert max(abs(x) for x in d1["mom"]) < 1e-4
+
+
+def test_block_steps_on_a_forest(cuda_lib):
+    """Block time-steps of a forest: with k_max = 0 they are bh_step bit for
+    bit; with several levels, each system's state matches stepping it alone."""
+    pos, vel, m, off = ics.ensemble(n_sys=6, seed=7, n_min=500, n_max=3000)
+    dt = 1.0 / 64
+
+    def run(p, v, mm, offsets, block, k_max=0, steps=3):
+        tc = cuda_lib.TreeCode(len(p), max(1, len(offsets) - 1) if offsets is not None else 1)
+        tc.set_state(_dev(p), _dev(v), _dev(mm), offsets=offsets)
+        if block:
+            tc.block_start(dt, k_max, 0.05, THETA, EPS)
+            while tc.block_info()["tick"] < steps * 2 ** k_max:
+                tc.block_step(THETA, EPS, rebuild=True)
+        else:
+            for _ in range(steps):
+                tc.step(dt, THETA, EPS, graph=False)
+        tc.check()
+        return _state(tc, len(p)), (_levels(tc) if block else None)
+
+    (a, _), (b, _) = run(pos, vel, m, off, False), run(pos, vel, m, off, True)
+    for u, w in zip(a, b):
+        assert np.array_equal(u, w)
+    # several levels: a forest's block steps treat each system on its own
+    (xf, vf, _), (lf, tf) = run(pos, vel, m, off, True, k_max=3, steps=1)
+    for s in (0, 3, 5):
+        lo, hi = off[s], off[s + 1]
+        (xs, vs, _), (ls, ts) = run(pos[lo:hi], vel[lo:hi], m[lo:hi], None, True, k_max=3, steps=1)
+        assert np.array_equal(lf[lo:hi], ls) and np.array_equal(tf[lo:hi], ts)
+        assert np.allclose(xf[lo:hi], xs, rtol=0, atol=1e-12) and np.allclose(vf[lo:hi], vs, rtol=0, atol=1e-9)
