@@ -681,9 +681,11 @@ __device__ __forceinline__ void pp2(Acc2 &a, const Targets2 &t, const float4 sh,
 
 // Softened particle-cell interaction, monopole + quadrupole, of one staged cell
 // with both slots of a lane, with d = com - target:
-//   a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7,  phi = -M/s - (d.Q.d)/(2 s^5).
-// 54 flops per slot by the convention above.  The staged Q is negated, so
-// q = -Q d and w = -d.Q.d come out of plain products.
+//   a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7,  phi = -M/s - (d.Q.d)/(2 s^5),
+// rearranged as a = (q + s^2 (M - (5/2) w/s^4) d)/s^5 with q = -Q d and
+// w = -d.Q.d (the staged Q is negated, so both come out of plain products):
+// 32 packed operations per slot pair, 53 flops per slot by the counting rule
+// (the work unit stays the 54 flops fixed from the first sequence).
 __device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0, const float4 q0, const float4 q1,
                                     float2 e2) {
   const float2 dx = __fadd2_rn(f2(c0.x, c0.x), t.nhx);
@@ -694,21 +696,22 @@ __device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0,
   r2 = __ffma2_rn(dz, dz, r2);
   const float2 ri = f2(rsqrtf(r2.x), rsqrtf(r2.y));
   const float2 ri2 = __fmul2_rn(ri, ri);
-  const float2 mr = __fmul2_rn(f2(c0.w, c0.w), ri);
-  const float2 mr3 = __fmul2_rn(mr, ri2);
+  const float2 M = f2(c0.w, c0.w);
   const float2 qxx = f2(q0.x, q0.x), qyy = f2(q0.y, q0.y), qzz = f2(q0.z, q0.z);
   const float2 qxy = f2(q0.w, q0.w), qxz = f2(q1.x, q1.x), qyz = f2(q1.y, q1.y);
   const float2 qx = __ffma2_rn(qxz, dz, __ffma2_rn(qxy, dy, __fmul2_rn(qxx, dx)));
   const float2 qy = __ffma2_rn(qyz, dz, __ffma2_rn(qyy, dy, __fmul2_rn(qxy, dx)));
   const float2 qz = __ffma2_rn(qzz, dz, __ffma2_rn(qyz, dy, __fmul2_rn(qxz, dx)));
   const float2 w = __ffma2_rn(qz, dz, __ffma2_rn(qy, dy, __fmul2_rn(qx, dx)));
-  const float2 ri5 = __fmul2_rn(__fmul2_rn(ri2, ri2), ri);
-  const float2 w5 = __fmul2_rn(w, ri5);
-  a.np = __ffma2_rn(f2(-0.5f, -0.5f), w5, __fadd2_rn(a.np, mr));
-  const float2 coef = __ffma2_rn(__fmul2_rn(f2(-2.5f, -2.5f), w5), ri2, mr3);
-  a.x = __ffma2_rn(qx, ri5, __ffma2_rn(coef, dx, a.x));
-  a.y = __ffma2_rn(qy, ri5, __ffma2_rn(coef, dy, a.y));
-  a.z = __ffma2_rn(qz, ri5, __ffma2_rn(coef, dz, a.z));
+  const float2 ri4 = __fmul2_rn(ri2, ri2);
+  const float2 ri5 = __fmul2_rn(ri4, ri);
+  const float2 u = __fmul2_rn(w, ri4);  // w / s^4
+  // a = (q + c d) / s^5 with c = s^2 (M - (5/2) u);  -phi += (M - u / 2) / s
+  const float2 c = __fmul2_rn(r2, __ffma2_rn(f2(-2.5f, -2.5f), u, M));
+  a.np = __ffma2_rn(__ffma2_rn(f2(-0.5f, -0.5f), u, M), ri, a.np);
+  a.x = __ffma2_rn(ri5, __ffma2_rn(c, dx, qx), a.x);
+  a.y = __ffma2_rn(ri5, __ffma2_rn(c, dy, qy), a.y);
+  a.z = __ffma2_rn(ri5, __ffma2_rn(c, dz, qz), a.z);
 }
 
 // Shared-memory staging: entries 32..kStage-1 are permanent nulls (zero mass, far away).
