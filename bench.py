@@ -489,7 +489,10 @@ def main():
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
     achieved = flops / eval_s if eval_s > 0 else 0.0  # the dominant kernel: k_eval
     achieved_walk = flops / walk_s if walk_s > 0 else 0.0
-    traffic = walk_traffic("eval_plummer_1m.md" if args.split else "walk_plummer_1m.md")
+    # the committed counters are of the 1M Plummer step at theta = 0.5 with the default options
+    profiled = (args.workload == "plummer" and args.n == N_BODIES and args.theta == THETA and args.mac == 0
+                and args.key_levels == 20 and not args.untuned and not args.list_capacity)
+    traffic = walk_traffic("eval_plummer_1m.md" if args.split else "walk_plummer_1m.md") if profiled else None
     clocks = clk.summary()
     mean_phase = {k: statistics.mean(p[k] for p in phases) for k in bh.PHASES if k != "call"}
     # build phases against HBM bandwidth
