@@ -192,6 +192,24 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _arg(t, dtype, what: str, cols: int = 0, cuda: bool = True, optional: bool = False):
+    """Pointer of a contiguous tensor of the given dtype (and row length) on
+    the GPU (or the host); raises before the library sees a wrong buffer."""
+    import torch
+
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{what}: a tensor is required")
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{what}: a contiguous {dtype} tensor is required")
+    if t.is_cuda != cuda:
+        raise ValueError(f"{what}: the tensor must be on the {'GPU' if cuda else 'host'}")
+    if cols and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{what}: shape [n, {cols}] is required")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream(stream):
     import torch
 
@@ -203,7 +221,10 @@ def _stream(stream):
 def default_params(**over) -> bh_params:
     p = bh_params()
     _check(load().bh_default_params(ctypes.byref(p)), "bh_default_params")
+    names = {f[0] for f in bh_params._fields_}
     for k, v in over.items():
+        if k not in names:
+            raise ValueError(f"unknown parameter {k!r} (bh_params has {sorted(names)})")
         setattr(p, k, int(v))
     return p
 
@@ -274,15 +295,19 @@ class TreeCode:
 
     # ---- force evaluation on device tensors (float64 pos [n,3], mass [n])
     def build(self, pos, mass, offsets=None, stream=None):
+        import torch
+
         n = pos.shape[0]
+        pp = _arg(pos, torch.float64, "pos", cols=3)
+        mp = _arg(mass, torch.float64, "mass")
         if offsets is None or len(offsets) <= 2:
-            _check(self.lib.bh_build(self.ctx, _ptr(pos), _ptr(mass), n, _stream(stream)), "bh_build")
+            _check(self.lib.bh_build(self.ctx, pp, mp, n, _stream(stream)), "bh_build")
         else:
             import numpy as np
 
             off = np.ascontiguousarray(offsets, dtype=np.int64)
-            _check(self.lib.bh_build_forest(self.ctx, _ptr(pos), _ptr(mass), n, off.ctypes.data_as(ctypes.c_void_p),
-                                            len(off) - 1, _stream(stream)), "bh_build_forest")
+            _check(self.lib.bh_build_forest(self.ctx, pp, mp, n, off.ctypes.data_as(ctypes.c_void_p), len(off) - 1,
+                                            _stream(stream)), "bh_build_forest")
 
     def compute_forces(self, theta: float, eps: float, acc=None, pot=None, stream=None):
         import torch
@@ -291,20 +316,29 @@ class TreeCode:
         if acc is None:
             acc = torch.empty((n, 3), dtype=torch.float32, device=f"cuda:{self.device}")
             pot = torch.empty(n, dtype=torch.float32, device=f"cuda:{self.device}")
-        _check(self.lib.bh_compute_forces(self.ctx, float(theta), float(eps), _ptr(acc), _ptr(pot), _stream(stream)),
+        _check(self.lib.bh_compute_forces(self.ctx, float(theta), float(eps), _arg(acc, torch.float32, "acc", cols=3),
+                                          _arg(pot, torch.float32, "pot"), _stream(stream)),
                "bh_compute_forces")
         return acc, pot
 
     def forces_host(self, pos, mass, theta: float, eps: float, acc, pot, stream=None):
         """pos/mass/acc/pot are (pinned) CPU tensors."""
-        _check(self.lib.bh_forces_host(self.ctx, _ptr(pos), _ptr(mass), pos.shape[0], float(theta), float(eps),
-                                       _ptr(acc), _ptr(pot), _stream(stream)), "bh_forces_host")
+        import torch
+
+        args = (_arg(pos, torch.float64, "pos", cols=3, cuda=False), _arg(mass, torch.float64, "mass", cuda=False))
+        outs = (_arg(acc, torch.float32, "acc", cols=3, cuda=False), _arg(pot, torch.float32, "pot", cuda=False))
+        _check(self.lib.bh_forces_host(self.ctx, *args, pos.shape[0], float(theta), float(eps), *outs,
+                                       _stream(stream)), "bh_forces_host")
 
     # ---- integration
     def set_state(self, pos, vel, mass, offsets=None, stream=None):
         import numpy as np
+        import torch
 
         n = pos.shape[0]
+        _arg(pos, torch.float64, "pos", cols=3)
+        _arg(vel, torch.float64, "vel", cols=3)
+        _arg(mass, torch.float64, "mass")
         if offsets is not None and len(offsets) > 2:
             off = np.ascontiguousarray(offsets, dtype=np.int64)
             optr, ns = off.ctypes.data_as(ctypes.c_void_p), len(off) - 1

@@ -54,3 +54,25 @@ def test_oracle_and_library_share_nothing():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src and "bh_oracle" not in src, f
+
+
+def test_binding_rejects_wrong_buffers_and_parameters():
+    """The binding checks argument buffers and parameter names before the
+    library sees them (argument marshalling only; no device needed)."""
+    import torch
+
+    import paper_1106_1900_gb300 as bh
+
+    ok = torch.zeros((4, 3), dtype=torch.float64)
+    assert bh._arg(ok, torch.float64, "pos", cols=3, cuda=False) is not None
+    for bad in (torch.zeros((4, 3), dtype=torch.float32), torch.zeros((3, 4), dtype=torch.float64).t(),
+                torch.zeros((4, 2), dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            bh._arg(bad, torch.float64, "pos", cols=3, cuda=False)
+    with pytest.raises(ValueError):
+        bh._arg(ok, torch.float64, "pos", cols=3, cuda=True)  # a host tensor where a device one is needed
+    with pytest.raises(ValueError):
+        bh._arg(None, torch.float64, "pos")
+    assert bh.default_params(n_crit=96, key_levels=30).n_crit == 96
+    with pytest.raises(ValueError):
+        bh.default_params(n_crti=96)
