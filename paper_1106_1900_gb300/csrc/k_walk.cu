@@ -30,9 +30,9 @@
 //  k_order     sorts the groups by their estimated evaluation cost (a
 //              logarithmic histogram filled by k_traverse, one scatter).
 //  k_eval      one warp per group, most expensive first, so that the launch
-//              ends on cheap groups.  Lists are read 32 entries at a time; the
-//              next tile's entries are gathered into registers while the
-//              current tile (staged in shared memory) is summed.
+//              ends on cheap groups.  Lists are summed 64 entries at a time:
+//              each lane gathers and stages two into shared memory, then every
+//              lane sums the tile from there.
 //
 // Slots: every lane holds two target slots, 64 per warp.  A group of n <= 32
 // bodies is laid out with h = ceil(n/2): lane l holds bodies l mod h and
@@ -76,11 +76,13 @@ constexpr int kWarps = 4;  // warps per block of both kernels
 constexpr int kThreads = 32 * kWarps;
 constexpr int kEvalMinBlocks = 6;
 constexpr int kWalkMinBlocks = 6;  // the fused walk (7 measured slower at N_crit = 96)
-// Staging entries per warp: a 32-entry tile plus permanent nulls.  With k
-// phases a lane reads entries ph, ph + k, ... < cnt + ph, the last one at most
-// k ceil(32 / k) - 1, and k = 32 / h is one of 1, 2, 3, 4, 5, 6, 8, 10, 16,
-// 32: at most entry 39 (k = 10).
-constexpr int kStage = 40;
+// Lists are summed in tiles of kTile entries, each lane staging two.  With k
+// phases a lane reads entries ph, ph + k, ... < cnt + ph, the last one at
+// most k ceil(64 / k) - 1, and k = 32 / h is one of 1, 2, 3, 4, 5, 6, 8, 10,
+// 16, 32: at most entry 69 (k = 10); entries 64..kStage-1 are permanent nulls.
+constexpr int kTile = 64;
+constexpr int kStage = 72;
+static_assert(kTile % 32 == 0 && kStage >= kTile + 6, "staging: whole warps per tile, nulls up to entry 69");
 // Interactions per slot between folds of the FP32 partial sums into the
 // compensated (hi, lo) pair: 64 (32 measured 1.5 % slower; a plain FP32 sum
 // of 64 terms is off by ~sqrt(64) ulp of its terms' magnitude, typically).
@@ -126,7 +128,7 @@ __host__ __device__ constexpr int slots_per_body(int n) { return 32 / pair_strid
 // bodies gets one slot per body and leaves 64 - n slots idle.  P passes over
 // subsets of ceil(n / P) bodies each, all on the group's own lists (a list
 // valid for a group is valid for any subset of it), fill the slots better.  A
-// pass costs ceil(32 / k) iterations per 32-entry tile, but no less than ~8:
+// pass costs ceil(32 / k) iterations per 32 list entries, but no less than ~8:
 // below that the tile's gather from L2 is no longer hidden behind its
 // arithmetic, and every pass re-gathers the lists.  So groups of up to 32
 // bodies keep one pass, 33..42 bodies take two, 43..48 three.  The rule is
@@ -718,17 +720,17 @@ __device__ __forceinline__ void pc2(Acc2 &a, const Targets2 &t, const float4 c0,
   a.z = __ffma2_rn(ri5, __ffma2_rn(c, dz, qz), a.z);
 }
 
-// Shared-memory staging: entries 32..kStage-1 are permanent nulls (zero mass, far away).
+// Shared-memory staging: entries kTile..kStage-1 are permanent nulls (zero mass, far away).
 __device__ __forceinline__ void init_stage(EvalSmem &S, int lane) {
   const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (lane < kStage - 32) {
-    S.sc[32 + lane][0] = null_src;
-    S.sc[32 + lane][1] = zero4;
-    S.sc[32 + lane][2] = zero4;
-    S.sp[32 + lane][0] = null_src;
-    S.sp[32 + lane][1] = zero4;
-    S.pidx[32 + lane] = -1;
+  if (lane < kStage - kTile) {
+    S.sc[kTile + lane][0] = null_src;
+    S.sc[kTile + lane][1] = zero4;
+    S.sc[kTile + lane][2] = zero4;
+    S.sp[kTile + lane][0] = null_src;
+    S.sp[kTile + lane][1] = zero4;
+    S.pidx[kTile + lane] = -1;
   }
   __syncwarp();
 }
@@ -782,48 +784,36 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
     t.x = t.y = t.z = t.np = f2(0.f, 0.f);
     int since = 0;  // interactions per slot since the last fold
 
-    // ---- cell list, 32 entries at a time; the next tile is gathered while this one is summed
+    // ---- cell list, kTile entries at a time (each lane stages two)
     {
-      // indices run one tile ahead of the gathers, which run one tile ahead of
-      // the arithmetic: no gather waits on the load of its own address
-      float4 ra = zero4, rb = zero4, rq0 = zero4, rq1 = zero4;
-      if (lane < nc) {
-        const size_t ci = clist[lane];
-        ra = A.mom[4 * ci];
-        rb = A.mom[4 * ci + 1];
-        rq0 = A.mom[4 * ci + 2];
-        rq1 = A.mom[4 * ci + 3];
-      }
-      uint32_t ci_next = (32 + lane < nc) ? clist[32 + lane] : 0u;
-      for (int base = 0; base < nc; base += 32) {
-        const int cnt = min(32, nc - base);
-        if (lane < cnt) {
-          float dx, dy, dz;
-          if (relative(VAR)) {
-            dx = (ra.x - cx) + rb.x;
-            dy = (ra.y - cy) + rb.y;
-            dz = (ra.z - cz) + rb.z;
+      for (int base = 0; base < nc; base += kTile) {
+        const int cnt = min(kTile, nc - base);
+#pragma unroll
+        for (int hh = 0; hh < kTile / 32; ++hh) {
+          const int e = hh * 32 + lane;
+          if (e < cnt) {
+            const size_t ci = clist[base + e];
+            const float4 ra = A.mom[4 * ci], rb = A.mom[4 * ci + 1], rq0 = A.mom[4 * ci + 2],
+                         rq1 = A.mom[4 * ci + 3];
+            float dx, dy, dz;
+            if (relative(VAR)) {
+              dx = (ra.x - cx) + rb.x;
+              dy = (ra.y - cy) + rb.y;
+              dz = (ra.z - cz) + rb.z;
+            } else {
+              dx = ra.x;
+              dy = ra.y;
+              dz = ra.z;
+            }
+            S.sc[e][0] = make_float4(dx, dy, dz, ra.w);
+            S.sc[e][1] = make_float4(-rq0.x, -rq0.y, -rq0.z, -rq0.w);
+            S.sc[e][2] = make_float4(-rq1.x, -rq1.y, 0.f, 0.f);
           } else {
-            dx = ra.x;
-            dy = ra.y;
-            dz = ra.z;
+            S.sc[e][0] = null_src;
+            S.sc[e][1] = zero4;
+            S.sc[e][2] = zero4;
           }
-          S.sc[lane][0] = make_float4(dx, dy, dz, ra.w);
-          S.sc[lane][1] = make_float4(-rq0.x, -rq0.y, -rq0.z, -rq0.w);
-          S.sc[lane][2] = make_float4(-rq1.x, -rq1.y, 0.f, 0.f);
-        } else {
-          S.sc[lane][0] = null_src;
-          S.sc[lane][1] = zero4;
-          S.sc[lane][2] = zero4;
         }
-        if (base + 32 + lane < nc) {  // gather the next tile now
-          const size_t ci = ci_next;
-          ra = A.mom[4 * ci];
-          rb = A.mom[4 * ci + 1];
-          rq0 = A.mom[4 * ci + 2];
-          rq1 = A.mom[4 * ci + 3];
-        }
-        if (base + 64 + lane < nc) ci_next = clist[base + 64 + lane];
         __syncwarp();
 #pragma unroll 1
         for (int j = ph; j < cnt + ph; j += k) {
@@ -838,36 +828,28 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
         __syncwarp();
       }
     }
-    // ---- particle list
+    // ---- particle list, kTile entries at a time (each lane stages two)
     {
-      float4 rh = zero4, rl = zero4;
-      int rb = -1;
-      if (lane < np) {
-        rb = (int)plist[lane];
-        rh = A.part_hi[rb];
-        rl = A.part_lo[rb];
-      }
-      int pb_next = (32 + lane < np) ? (int)plist[32 + lane] : -1;
-      for (int base = 0; base < np; base += 32) {
-        const int cnt = min(32, np - base);
+      for (int base = 0; base < np; base += kTile) {
+        const int cnt = min(kTile, np - base);
         bool member = false;
-        if (lane < cnt) {
-          member = (unsigned)(rb - gb) < (unsigned)n;
-          const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
-          S.sp[lane][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
-          S.sp[lane][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
-          S.pidx[lane] = rb;
-        } else {
-          S.sp[lane][0] = null_src;
-          S.sp[lane][1] = zero4;
-          S.pidx[lane] = -1;
+#pragma unroll
+        for (int hh = 0; hh < kTile / 32; ++hh) {
+          const int e = hh * 32 + lane;
+          if (e < cnt) {
+            const int rb = (int)plist[base + e];
+            const float4 rh = A.part_hi[rb], rl = A.part_lo[rb];
+            member |= (unsigned)(rb - gb) < (unsigned)n;
+            const Target s = make_target<VAR>(rh, rl, cx, cy, cz);
+            S.sp[e][0] = make_float4(s.hx, s.hy, s.hz, rh.w);
+            S.sp[e][1] = make_float4(s.lx, s.ly, s.lz, 0.f);
+            S.pidx[e] = rb;
+          } else {
+            S.sp[e][0] = null_src;
+            S.sp[e][1] = zero4;
+            S.pidx[e] = -1;
+          }
         }
-        if (base + 32 + lane < np) {  // gather the next tile now
-          rb = pb_next;
-          rh = A.part_hi[rb];
-          rl = A.part_lo[rb];
-        }
-        if (base + 64 + lane < np) pb_next = (int)plist[base + 64 + lane];
         const bool self_tile = __any_sync(kFull, member);
         __syncwarp();
         if (self_tile) {
