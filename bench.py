@@ -188,9 +188,12 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(pos, mass, theta, eps, n_leaf=16, n_crit=64, target_s=15.0):
+def cpu_baseline(pos, mass, theta, eps, n_leaf=16, n_crit=64, target_s=15.0, gpu=None):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload
-    (same N_leaf, N_crit): the whole tree build plus the walk of every k-th group."""
+    (same N_leaf, N_crit): the whole tree build plus the walk of every k-th group.
+    With ``gpu`` = (acc, pot, group stats) of the library's force evaluation of
+    the same input, also the parity report of the sampled groups (the policy
+    of the parity tests: 1e-5 per body, clauses counted and bounded)."""
     import numpy as np
 
     import oracle
@@ -207,15 +210,29 @@ def cpu_baseline(pos, mass, theta, eps, n_leaf=16, n_crit=64, target_s=15.0):
     k = max(1, int(t.G * per_group / max(target_s - t_build, 1.0)))
     groups = np.arange(0, t.G, k)
     t0 = time.perf_counter()
-    oracle.walk(t, theta, eps, groups)
+    acc_s, pot_s, st = oracle.walk(t, theta, eps, groups)
     t_walk = time.perf_counter() - t0
     bodies = int(sum(t.gend[g] - t.gbeg[g] for g in groups))
     secs = t_walk + t_build * bodies / t.n
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": bodies / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 tree build of all {t.n} bodies ({t_build:.2f} s, charged pro rata) + walk of "
-                      f"every {k}-th group ({len(groups)} groups, {bodies} bodies, {t_walk:.2f} s), "
-                      f"theta={theta}, eps={eps}, N_leaf={n_leaf}, N_crit={n_crit}"}
+    out = {"value": bodies / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"FP64 tree build of all {t.n} bodies ({t_build:.2f} s, charged pro rata) + walk of "
+                     f"every {k}-th group ({len(groups)} groups, {bodies} bodies, {t_walk:.2f} s), "
+                     f"theta={theta}, eps={eps}, N_leaf={n_leaf}, N_crit={n_crit}"}
+    if gpu is not None:
+        from tests import _parity
+
+        acc_g, pot_g, gst = gpu
+        try:
+            rep = _parity.group_forces_report(acc_g, pot_g, t, groups, acc_s, pot_s, st,
+                                              {k_: v[groups] for k_, v in gst.items()})
+            rep["ok"] = True
+        except AssertionError as e:
+            rep = {"ok": False, "error": str(e)[:500]}
+        rep["what"] = (f"library forces vs the FP64 oracle on the same tree, the {len(groups)} sampled groups "
+                       f"({bodies} bodies) of the initial state: tolerance 1e-5 per body")
+        out["parity"] = rep
+    return out
 
 
 def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, k_max=6, eta=0.05,
@@ -535,7 +552,15 @@ def main():
                "refresh_inside": block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pos, m, args.theta, eps, tc.params.n_leaf, tc.params.n_crit)
+        # the library's forces on the initial state, for the parity report of the sampled groups
+        tcp = bh.TreeCode(n, device=local, **kw)
+        tcp.build(torch.from_numpy(pos).to(dev), torch.from_numpy(m).to(dev))
+        acc0, pot0 = tcp.compute_forces(args.theta, eps)
+        tcp.check()
+        gpu0 = (acc0.cpu().numpy(), pot0.cpu().numpy(), tcp.group_stats())
+        tcp.close()
+        del acc0, pot0
+        cpu = cpu_baseline(pos, m, args.theta, eps, tc.params.n_leaf, tc.params.n_crit, gpu=gpu0)
     if rank != 0:
         return
     cnt = tc.counts()
@@ -570,7 +595,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
-        "cpu_baseline": cpu,
+        "cpu_baseline": {k_: v for k_, v in cpu.items() if k_ != "parity"} if cpu else None,
+        "parity": cpu.get("parity") if cpu else None,
         "ensemble": ens,
         "block": blk,
         "wall_s_timed": wall1 - wall0,

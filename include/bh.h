@@ -67,7 +67,10 @@ typedef struct bh_params {
     int32_t list_capacity;  /* longest cell list and longest particle list of one
                                group (§2.2 interaction lists), default 16384 */
     int32_t pool_per_body;  /* interaction-list pool entries per body (the lists of
-                               all groups of one walk, split walk only), default 768 */
+                               all groups of one walk, split walk only), default 768;
+                               a pool above 2^34 entries (pool_per_body x n_max)
+                               is refused with BH_ERR_CAPACITY at bh_create and
+                               bh_workspace_bytes */
     int32_t walk_split;     /* 0: one fused kernel walks each group and evaluates its
                                lists from the walking warp's scratch (default);
                                1: a walk kernel writes every group's lists to the pool,
@@ -267,8 +270,8 @@ int bh_phase_times(bh_ctx *ctx, float ms[BH_NPHASES]);
 int bh_walk_time(bh_ctx *ctx, float *ms);
 
 /* App. A scan primitive (device-wide exclusive prefix sum of uint32), exposed
- * for verification: out_dev[i] = in_dev[0] + ... + in_dev[i-1], and
- * *total_host = the sum of all n values (synchronises).  Needs a bound
+ * for verification: out_dev[i] = in_dev[0] + ... + in_dev[i-1] modulo 2^32,
+ * and *total_host = the exact sum of all n values (synchronises).  Needs a bound
  * workspace and n <= n_max. */
 int bh_prim_exclusive_scan(bh_ctx *ctx, const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_host,
                            void *stream);
@@ -291,18 +294,22 @@ int bh_direct_forces(const double *pos_dev, const double *mass_dev, int64_t n, c
  * workspace.  It needs no context.
  *
  * in_dev[n], out_dev[n] (uint32, device): out_dev[i] = in_dev[0] + ... +
- * in_dev[i-1].  total_dev (device, may be NULL): receives the sum of all n
- * values as uint64.  Stream-ordered, no host synchronisation.
+ * in_dev[i-1] modulo 2^32.  total_dev (device, may be NULL): receives the
+ * exact sum of all n values as uint64 (0 for n = 0).  Stream-ordered, no host
+ * synchronisation.
  *
- * Its only scratch is a fixed array compiled into the library (64 KiB +
+ * Its only scratch is a fixed array compiled into the library (128 KiB +
  * 8 bytes), held by every GPU that loads the library until the process
  * exits.  It allocates nothing, so n is limited to BH_NOALLOC_SCAN_MAX_N:
  * larger n returns BH_ERR_CAPACITY before anything is launched.  The first
  * call on each device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call
- * shares the one array (no call relies on what an earlier call left in it),
- * so calls that overlap on the GPU -- on different streams, or from
- * different host threads -- race: serialise them. */
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this entry point again on a
+ * device after cudaDeviceReset of that device (the kept address is then
+ * stale).  Every call shares the one array (no call relies on what an
+ * earlier call left in it), so calls that overlap on the GPU -- on
+ * different streams, or from different host threads -- race: serialise
+ * them. */
 #define BH_NOALLOC_SCAN_MAX_N (1ll << 26)
 int bh_exclusive_scan_noalloc(const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_dev,
                               void *stream);

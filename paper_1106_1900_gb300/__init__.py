@@ -229,6 +229,14 @@ def default_params(**over) -> bh_params:
     return p
 
 
+def workspace_bytes(params: bh_params, n_max: int, n_sys_max: int = 1, device: int = 0) -> int:
+    """Device workspace bytes of a context (``bh_workspace_bytes``)."""
+    nbytes = ctypes.c_size_t(0)
+    _check(load().bh_workspace_bytes(ctypes.byref(params), n_max, n_sys_max, device, ctypes.byref(nbytes)),
+           "bh_workspace_bytes")
+    return nbytes.value
+
+
 def fp32_peak(device: int = 0, iters: int = 4096, stream=None) -> float:
     """Measured FP32 FMA throughput (FLOP/s) of the device."""
     out = ctypes.c_double(0)
@@ -250,16 +258,30 @@ def direct_forces(pos, mass, targets, eps: float, stream=None):
 
 
 def exclusive_scan_noalloc(x, out=None, total=None, stream=None):
-    """Exclusive prefix sum of a uint32/int32 CUDA tensor through
+    """Exclusive prefix sum of a contiguous int32 CUDA tensor through
     ``bh_exclusive_scan_noalloc`` (no context, no workspace; the library
-    allocates nothing).  ``total``, if given, is a 1-element int64 CUDA tensor
-    that receives the sum."""
+    allocates nothing).  The values are read as uint32 and the prefix sums
+    wrap modulo 2^32.  ``total``, if given, is a contiguous 1-element int64
+    CUDA tensor on the same device that receives the exact sum (as uint64
+    bits).  The call runs with ``x``'s device current, on ``stream`` (that
+    device's current stream by default)."""
     import torch
 
+    _arg(x, torch.int32, "x")
     if out is None:
         out = torch.empty_like(x)
-    _check(load().bh_exclusive_scan_noalloc(_ptr(x), _ptr(out), x.numel(), _ptr(total), _stream(stream)),
-           "bh_exclusive_scan_noalloc")
+    _arg(out, torch.int32, "out")
+    _arg(total, torch.int64, "total", optional=True)
+    if out.numel() != x.numel():
+        raise ValueError("out: as many elements as x are required")
+    if total is not None and total.numel() != 1:
+        raise ValueError("total: one element is required")
+    for t in (out, total):
+        if t is not None and t.device != x.device:
+            raise ValueError("out and total must be on x's device")
+    with torch.cuda.device(x.device):
+        _check(load().bh_exclusive_scan_noalloc(_ptr(x), _ptr(out), x.numel(), _ptr(total), _stream(stream)),
+               "bh_exclusive_scan_noalloc")
     return out
 
 

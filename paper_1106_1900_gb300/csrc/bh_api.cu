@@ -91,6 +91,8 @@ int plan(Ctx &c, const bh_params *p, int64_t n_max, int32_t s_max, int device) {
   c.trav_warps_total = (fused ? c.walk_grid : c.trav_grid) * bh::walk_block_warps();
   // the list pool serves the split walk only
   c.pool_cap = fused ? 32 : std::max<int64_t>((int64_t)p->pool_per_body * n_max, 1ll << 22);
+  // group offsets into the pool are stored as 32-bit multiples of kPoolAlign
+  if (c.pool_cap > ((int64_t)bh::kPoolAlign << 32)) return BH_ERR_CAPACITY;
   c.sort_max_passes = bh::sort_passes_for(s_max, c.levels);
   c.sort_tiles_max = bh::sort_tiles_for(n_max);
   return BH_OK;
@@ -155,7 +157,7 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.sort_hist = k.take<uint32_t>((size_t)c.sort_max_passes * 256);
   c.sort_status = k.take<uint32_t>((size_t)c.sort_max_passes * c.sort_tiles_max * 256);
   c.sort_tile_ctr = k.take<uint32_t>((size_t)c.sort_max_passes);
-  c.scan_blocks = k.take<uint32_t>(std::max(R, N) / 4096 + 2);
+  c.scan_blocks = k.take<uint64_t>(std::max(R, N) / 4096 + 2);
   c.scan_total = k.take<uint64_t>(1);
   c.walk_stack = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.stack_capacity);
   c.list_scratch = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.list_capacity);

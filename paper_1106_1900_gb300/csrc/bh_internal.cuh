@@ -15,6 +15,7 @@ constexpr int kRowsMax = kLevelsMax + 2;  // cell levels 0..D + one row of group
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kCostBuckets = 256;  // logarithmic buckets of a group's estimated evaluation cost
 constexpr int kMaxCrit = 256;      // largest group size N_crit (the level build's window halo)
+constexpr int kPoolAlign = 4;      // split walk: list-pool offsets in units of 4 entries (2^34 entries addressable)
 
 // Frame of one system: origin (per-axis minimum) and power-of-two side L.
 struct __align__(32) Frame {
@@ -110,7 +111,7 @@ struct Ctx {
   int sort_max_passes = 0;
   int64_t sort_tiles_max = 0;
   // scan scratch
-  uint32_t *scan_blocks;         // [blocks]
+  uint64_t *scan_blocks;         // [blocks] exact 64-bit block sums of the scan
   uint64_t *scan_total;          // [1]
   // walk
   int32_t *walk_stack;           // [traversal warps][2][stack_capacity]
@@ -153,7 +154,7 @@ cudaError_t launch_wait_probe(Ctx &c, int limit, cudaStream_t s);  // failure pa
 cudaError_t launch_move_state(Ctx &c, cudaStream_t s);  // gather state cur -> other, fills part_hi/lo
 cudaError_t launch_cells(Ctx &c, cudaStream_t s);
 cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
-cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *blocks, uint64_t *total,
+cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *blocks, uint64_t *total,
                                 cudaStream_t s);
 int64_t scan_blocks_for(int64_t n);
 // k_moments.cu

@@ -749,10 +749,13 @@ __global__ void __launch_bounds__(kBlock) k_link(int n, const uint64_t *__restri
 constexpr int kScanIpt = 16;
 constexpr int kScanTile = kBlock * kScanIpt;
 
-__global__ void __launch_bounds__(kBlock) k_scan_up(const uint32_t *__restrict__ in, int64_t n, uint32_t *blocks) {
-  __shared__ uint32_t s_w[kBlock / 32];
+// Block sums are exact 64-bit sums (a tile of 4096 values below 2^32 sums
+// below 2^44), so the total is exact; the scanned values themselves wrap
+// modulo 2^32, the width of the output.
+__global__ void __launch_bounds__(kBlock) k_scan_up(const uint32_t *__restrict__ in, int64_t n, uint64_t *blocks) {
+  __shared__ uint64_t s_w[kBlock / 32];
   const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
-  uint32_t sum = 0;
+  uint64_t sum = 0;
   for (int j = 0; j < kScanIpt; ++j) {
     int64_t i = b0 + j * kBlock + threadIdx.x;
     if (i < n) sum += in[i];
@@ -761,39 +764,40 @@ __global__ void __launch_bounds__(kBlock) k_scan_up(const uint32_t *__restrict__
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t t = 0;
+    uint64_t t = 0;
     for (int w = 0; w < kBlock / 32; ++w) t += s_w[w];
     blocks[blockIdx.x] = t;
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_mid(uint32_t *blocks, int nb, uint64_t *total) {
-  __shared__ uint32_t s_w[32];
-  __shared__ uint32_t s_carry;
+// Exclusive scan of the nb block sums in place, in 64 bits; *total = their sum.
+__global__ void __launch_bounds__(1024) k_scan_mid(uint64_t *blocks, int nb, uint64_t *total) {
+  __shared__ uint64_t s_w[32];
+  __shared__ uint64_t s_carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   for (int base = 0; base < nb; base += 1024) {
     int i = base + threadIdx.x;
-    uint32_t v = (i < nb) ? blocks[i] : 0;
-    uint32_t x = v;
+    uint64_t v = (i < nb) ? blocks[i] : 0;
+    uint64_t x = v;
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(kFull, x, o);
+      uint64_t y = __shfl_up_sync(kFull, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) s_w[warp] = x;
     __syncthreads();
     if (warp == 0) {
-      uint32_t w = s_w[lane];
+      uint64_t w = s_w[lane];
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(kFull, w, o);
+        uint64_t y = __shfl_up_sync(kFull, w, o);
         if (lane >= o) w += y;
       }
       s_w[lane] = w;
     }
     __syncthreads();
-    uint32_t carry = s_carry;
-    uint32_t excl = carry + (warp ? s_w[warp - 1] : 0) + x - v;
+    uint64_t carry = s_carry;
+    uint64_t excl = carry + (warp ? s_w[warp - 1] : 0) + x - v;
     if (i < nb) blocks[i] = excl;
     __syncthreads();
     if (threadIdx.x == 0) s_carry = carry + s_w[31];
@@ -803,7 +807,7 @@ __global__ void __launch_bounds__(1024) k_scan_mid(uint32_t *blocks, int nb, uin
 }
 
 __global__ void __launch_bounds__(kBlock) k_scan_down(const uint32_t *__restrict__ in, int64_t n,
-                                                      const uint32_t *__restrict__ blocks, uint32_t *out) {
+                                                      const uint64_t *__restrict__ blocks, uint32_t *out) {
   __shared__ uint32_t s[kScanTile];
   __shared__ uint32_t s_w[kBlock / 32];
   const int64_t b0 = (int64_t)blockIdx.x * kScanTile;
@@ -828,7 +832,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_down(const uint32_t *__restrict
   __syncthreads();
   uint32_t wb = 0;
   for (int w = 0; w < warp; ++w) wb += s_w[w];
-  const uint32_t base = blocks[blockIdx.x] + wb + x - sum;
+  const uint32_t base = (uint32_t)blocks[blockIdx.x] + wb + x - sum;
   __syncthreads();
   for (int j = 0; j < kScanIpt; ++j) s[threadIdx.x * kScanIpt + j] = base + loc[j];
   __syncthreads();
@@ -983,8 +987,9 @@ cudaError_t launch_scan_u32(Ctx &c, const uint32_t *in, uint32_t *out, int64_t n
 }
 
 // The same three scan kernels with caller-chosen scratch: `blocks` holds
-// scan_blocks_for(n) block sums, `total` receives the sum of all n values.
-cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *blocks, uint64_t *total,
+// scan_blocks_for(n) 64-bit block sums, `total` receives the exact sum of all n
+// values (out wraps modulo 2^32).
+cudaError_t launch_scan_u32_raw(const uint32_t *in, uint32_t *out, int64_t n, uint64_t *blocks, uint64_t *total,
                                 cudaStream_t s) {
   int nb = cdiv(n, kScanTile);
   if (nb == 0) return cudaMemsetAsync(total, 0, sizeof(uint64_t), s);

@@ -10,7 +10,7 @@
 // the library.
 //
 // The array lives in every GPU that loads the library until the process
-// exits (64 KiB + 8 bytes).  Host code cannot use the array's name as a
+// exits (128 KiB + 8 bytes: 16,384 64-bit block sums and the total).  Host code cannot use the array's name as a
 // device address -- in host code it names a host-side stand-in -- so the
 // first call on each device asks the runtime for the array's device address
 // (cudaGetSymbolAddress, with that device current) and caches it.
@@ -25,9 +25,9 @@ namespace {
 constexpr int64_t kMaxN = BH_NOALLOC_SCAN_MAX_N;
 constexpr int kMaxDevices = 64;
 
-// block sums of the largest scan, then one 64-bit total
+// 64-bit block sums of the largest scan (4096 values a block), then the total
 constexpr int64_t kMaxBlocks = (kMaxN + 4095) / 4096;
-static __device__ __align__(256) uint32_t g_scan_scratch[kMaxBlocks + 2];
+static __device__ __align__(256) uint64_t g_scan_scratch[kMaxBlocks + 1];
 
 std::mutex g_mutex;
 void *g_scratch_addr[kMaxDevices] = {};
@@ -61,9 +61,9 @@ extern "C" int bh_exclusive_scan_noalloc(const uint32_t *in_dev, uint32_t *out_d
   void *scratch = nullptr;
   int rc = scratch_on_current_device(&scratch);
   if (rc) return rc;
-  uint32_t *blocks = static_cast<uint32_t *>(scratch);
-  // the total goes to the caller's buffer, else to the array's last 8 bytes
-  uint64_t *total = total_dev ? total_dev : reinterpret_cast<uint64_t *>(blocks + kMaxBlocks);
+  uint64_t *blocks = static_cast<uint64_t *>(scratch);
+  // the total goes to the caller's buffer, else to the array's last element
+  uint64_t *total = total_dev ? total_dev : blocks + kMaxBlocks;
   cudaError_t e = bh::launch_scan_u32_raw(in_dev, out_dev, n, blocks, total, (cudaStream_t)stream);
   return e == cudaSuccess ? BH_OK : BH_ERR_CUDA;
 }

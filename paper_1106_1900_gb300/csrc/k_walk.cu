@@ -487,10 +487,12 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       full = true;
       if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
     }
-    // ---- copy the lists into the pool at an exact offset
+    // ---- copy the lists into the pool at an exact offset, a multiple of
+    // kPoolAlign entries so that offset / kPoolAlign fits the 32-bit field
     const int nc = min(w.ncell, A.list_cap), npp = min(w.npart, A.list_cap);
     unsigned long long off = 0;
-    if (lane == 0) off = atomicAdd(A.pool_ctr, (unsigned long long)(nc + npp));
+    if (lane == 0)
+      off = atomicAdd(A.pool_ctr, (unsigned long long)((nc + npp + kPoolAlign - 1) / kPoolAlign * kPoolAlign));
     off = __shfl_sync(kFull, off, 0);
     if (off + (unsigned long long)(nc + npp) > A.pool_cap) {
       full = true;
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       const int P = eval_passes(n);
       const int k = slots_per_body((n + P - 1) / P);
       const int work = full ? 1 : P * ((2 * nc + npp + k - 1) / k + 1);
-      A.g_list[g] = full ? make_int4(0, 0, 0, work) : make_int4((int)off, nc, npp, work);
+      A.g_list[g] = full ? make_int4(0, 0, 0, work) : make_int4((int)(unsigned)(off / kPoolAlign), nc, npp, work);
       atomicAdd(&A.work_hist[cost_bucket(work)], 1u);
       record_group(A, g, n, w);
     }
@@ -938,7 +940,7 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     const int g = A.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
     const int4 L = A.g_list[g];
-    const uint32_t *lst = A.pool + (unsigned)L.x;
+    const uint32_t *lst = A.pool + (size_t)kPoolAlign * (unsigned)L.x;
     // pull the group's lists from DRAM into L2 now (one 128-byte line per 32 entries)
     for (int i = 32 * lane; i < L.y + L.z; i += 32 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(lst + i));
     eval_group<VAR, GUARD, MODE>(A, S, lane, g, lst, L.y, lst + L.y, L.z);
@@ -1000,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_f64(EvalArgs A) {
     const int gb = A.g_beg[g];
     const int n = A.g_beg[g + 1] - gb;
     const int4 L = A.g_list[g];
-    const uint32_t *clist = A.pool + (unsigned)L.x;
+    const uint32_t *clist = A.pool + (size_t)kPoolAlign * (unsigned)L.x;
     const uint32_t *plist = clist + L.y;
     for (int b = lane; b < n; b += 32) {  // (one sweep: this study variant is not tuned)
       const float4 th = A.part_hi[gb + b], tl = A.part_lo[gb + b];

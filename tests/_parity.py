@@ -15,6 +15,8 @@ Forces follow this policy:
   oracle must have met a decision that close to its threshold (relative
   margin < MARGIN), and those bodies are held to FLIP_TOL = 1e-3 (the tree's
   own approximation error).
+* Neither exception may be common: the bodies that needed the conditioning
+  term and the groups with a flipped decision are counted and bounded.
 """
 import numpy as np
 
@@ -27,6 +29,14 @@ U_TERM = 8 * 2.0 ** -24
 KAPPA = U_TERM / TOL  # ~0.048
 MARGIN = 1e-5
 FLIP_TOL = 1e-3
+# At most this fraction of the compared bodies may need the conditioning clause
+# (their |a| below KAPPA * sum_j |a_ij|: near the centre of a cluster), and at
+# most this fraction of the compared groups may have a flipped decision; the
+# absolute floors serve small inputs.
+MAX_COND_FRAC = 1e-3
+MIN_COND = 4
+MAX_FLIP_FRAC = 5e-3
+MIN_FLIP = 2
 
 
 def group_of_sorted(gbeg, n):
@@ -66,37 +76,59 @@ def compare_moments(mom, t, tol=2e-6):
     return {"com": float(com_err.max()), "quad": float(q_err.max()), "delta": float(d_err.max())}
 
 
-def compare_forces(acc_g, pot_g, acc_o, pot_o, t, st_o, st_g, tol=TOL):
-    """Accelerations and potentials (input order) under the policy above."""
-    n = t.n
+def group_forces_report(acc_in, pot_in, t, groups, acc_s, pot_s, st_o, st_g, tol=TOL):
+    """Forces of the listed groups under the policy above.
+
+    ``acc_in``/``pot_in``: the GPU's results in input order; ``acc_s``,
+    ``pot_s``, ``st_o``: the oracle's walk of ``groups`` (sorted order, stats
+    per listed group); ``st_g``: the GPU's group statistics of the same groups.
+    Besides the per-body bounds it bounds how many bodies needed the
+    conditioning clause (at most MAX_COND_FRAC of the compared bodies) and how
+    many groups had an opening decision flip (at most MAX_FLIP_FRAC of them),
+    so that neither clause can cover a systematic error."""
+    groups = np.asarray(groups, dtype=np.int64)
     same = ((st_g["nc"] == st_o["nc"]) & (st_g["np"] == st_o["np"]) & (st_g["csum"] == st_o["csum"])
             & (st_g["psum"] == st_o["psum"]))
     flipped = np.nonzero(~same)[0]
     assert np.all(st_o["margin"][flipped] < MARGIN), (
-        f"groups {flipped[st_o['margin'][flipped] >= MARGIN][:10]} have different lists without a near-tie")
-    gs = group_of_sorted(t.gbeg, n)
-    g_in = np.empty(n, dtype=np.int64)
-    g_in[t.perm] = gs
-    ok_body = same[g_in]
-    an = np.linalg.norm(acc_o, axis=1)
-    amag = st_o["amag_input_order"]
+        f"groups {groups[flipped[st_o['margin'][flipped] >= MARGIN][:10]]} have different lists without a near-tie")
+    sizes = t.gend[groups] - t.gbeg[groups]
+    bodies = np.concatenate([np.arange(t.gbeg[g], t.gend[g]) for g in groups]) if len(groups) else np.zeros(0, int)
+    ok_body = np.repeat(same, sizes)
+    inp = t.perm[bodies]
+    ao = acc_s[bodies]
+    an = np.linalg.norm(ao, axis=1)
+    amag = st_o["amag"][bodies]
     scale = np.maximum(an, KAPPA * amag)
-    da = np.linalg.norm(acc_g.astype(np.float64) - acc_o, axis=1)
+    da = np.linalg.norm(acc_in[inp].astype(np.float64) - ao, axis=1)
     rel = da / np.maximum(scale, 1e-300)
-    prel = np.abs(pot_g.astype(np.float64) - pot_o) / np.maximum(np.abs(pot_o), 1e-300)
+    po = pot_s[bodies]
+    prel = np.abs(pot_in[inp].astype(np.float64) - po) / np.maximum(np.abs(po), 1e-300)
     plain = da / np.maximum(an, 1e-300)
+    any_ok = bool(ok_body.any())
     rep = {
-        "groups": int(len(same)), "flipped_groups": int(len(flipped)),
-        "max_rel": float(rel[ok_body].max()) if ok_body.any() else 0.0,
-        "max_prel": float(prel[ok_body].max()) if ok_body.any() else 0.0,
-        "p99_plain": float(np.percentile(plain[ok_body], 99)) if ok_body.any() else 0.0,
-        "max_plain": float(plain[ok_body].max()) if ok_body.any() else 0.0,
+        "groups": int(len(groups)), "bodies": int(len(bodies)), "flipped_groups": int(len(flipped)),
+        "max_rel": float(rel[ok_body].max()) if any_ok else 0.0,
+        "max_prel": float(prel[ok_body].max()) if any_ok else 0.0,
+        "p99_plain": float(np.percentile(plain[ok_body], 99)) if any_ok else 0.0,
+        "max_plain": float(plain[ok_body].max()) if any_ok else 0.0,
         "n_conditioned": int(np.sum(ok_body & (plain > tol))),
-        "worst_cond": float((an / np.maximum(amag, 1e-300))[ok_body][np.argmax(rel[ok_body])]) if ok_body.any()
-        else 0.0,
+        "worst_cond": float((an / np.maximum(amag, 1e-300))[ok_body][np.argmax(rel[ok_body])]) if any_ok else 0.0,
         "flip_max": float(rel[~ok_body].max()) if (~ok_body).any() else 0.0,
     }
     assert rep["max_rel"] <= tol, f"acceleration error {rep}"
     assert rep["max_prel"] <= tol, f"potential error {rep}"
     assert rep["flip_max"] <= FLIP_TOL, f"flipped-group error {rep}"
+    assert rep["n_conditioned"] <= max(MIN_COND, MAX_COND_FRAC * rep["bodies"]), f"conditioning clause overused {rep}"
+    assert rep["flipped_groups"] <= max(MIN_FLIP, MAX_FLIP_FRAC * rep["groups"]), f"too many flipped groups {rep}"
     return rep
+
+
+def compare_forces(acc_g, pot_g, acc_o, pot_o, t, st_o, st_g, tol=TOL):
+    """Accelerations and potentials of every group (GPU and oracle results in
+    input order, ``st_o`` from ``oracle.tree_forces``)."""
+    acc_s = np.empty_like(acc_o)
+    pot_s = np.empty_like(pot_o)
+    acc_s[np.arange(t.n)] = acc_o[t.perm]
+    pot_s[np.arange(t.n)] = pot_o[t.perm]
+    return group_forces_report(acc_g, pot_g, t, np.arange(t.G), acc_s, pot_s, st_o, st_g, tol)

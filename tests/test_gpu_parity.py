@@ -172,6 +172,16 @@ def test_stack_overflow_is_reported(cuda_lib):
     assert tc.status() == 0  # the status word was cleared
 
 
+def test_list_pool_above_its_address_range_is_refused(cuda_lib):
+    # the split walk addresses its list pool with 32-bit multiples of 4
+    # entries: a pool above 2^34 entries is refused before anything is bound
+    p = cuda_lib.default_params(walk_split=1, pool_per_body=4096)
+    with pytest.raises(cuda_lib.BHError) as e:
+        cuda_lib.workspace_bytes(p, 1 << 23)
+    assert e.value.code == 2  # BH_ERR_CAPACITY
+    cuda_lib.workspace_bytes(cuda_lib.default_params(walk_split=1, pool_per_body=2048), 1 << 23)
+
+
 def test_bounded_wait_gives_up(cuda_lib):
     # a look-back wait on tiles that nothing publishes gives up, latches the
     # timeout and leaves the context usable
@@ -269,6 +279,26 @@ def test_two_body_orbit_energy(cuda_lib):
     assert np.max(np.abs(x - pos)) < 1e-3
 
 
+def test_diagnostics_match_oracle(cuda_lib):
+    """Energies and momentum (§4.2.2, Eq. 3) of a 16K Plummer state after one
+    step, against the oracle's energy and momentum of the same positions and
+    velocities with the oracle tree's potentials (same N_leaf, N_crit)."""
+    pos, vel, m = ics.plummer(16384, 34)
+    m = m * np.random.default_rng(34).uniform(0.5, 1.5, len(m))
+    tc, x, v, a, p = _state_run(cuda_lib, pos, vel, m, 1, 1 / 64, 0.5, 0.01)
+    d = tc.diagnostics()
+    _, pot_o, _, _ = oracle.tree_forces(x, m, 0.5, 0.01)
+    ek, ep, _ = oracle.energy(v, m, pot_o)
+    mom = oracle.momentum(v, m)
+    assert abs(d["ekin"] - ek) <= 1e-6 * abs(ek)
+    assert abs(d["epot"] - ep) <= 1e-5 * abs(ep)
+    scale = float(np.sum(m * np.linalg.norm(v, axis=1)))
+    assert np.linalg.norm(np.array(d["mom"]) - mom) <= 1e-6 * scale
+    # the kinetic energy and momentum are FP64 sums of the state: much closer
+    assert abs(d["ekin"] - ek) <= 1e-12 * abs(ek)
+    assert np.linalg.norm(np.array(d["mom"]) - mom) <= 1e-12 * scale
+
+
 def test_graph_step_equals_eager(cuda_lib):
     pos, vel, m = ics.plummer(20000, 32)
     _, x1, v1, a1, _ = _state_run(cuda_lib, pos, vel, m, 4, 1 / 64, 0.5, 0.01, graph=False)
@@ -334,49 +364,51 @@ def test_forest_step_equals_systems(cuda_lib):
         assert np.allclose(vf[b:e], vs, rtol=0, atol=1e-9)
 
 
-# --------------------------------------------- full-size workloads, sampled
-def _sampled_parity(bh, pos, m, theta, eps, every, offsets=None, **kw):
-    """Integer tables bit-exact; forces of every `every`-th group against the
-    oracle walking the same groups (the launch configuration of bench.py)."""
-    tc, acc, pot = _run(bh, pos, m, theta, eps, offsets=offsets, **kw)
-    t = oracle.build_tree(pos, m, offsets=offsets)
+# --------------------------------------------- full-size workloads
+def _workload_parity(bh, pos, m, theta, eps, kind, every=1, offsets=None, **kw):
+    """The benchmark's launch configuration (autotuned N_leaf, N_crit of the
+    workload class): integer tables bit-exact, moments of every cell, and the
+    forces of every `every`-th group (all of them by default) against the
+    oracle walking the same groups."""
+    from paper_1106_1900_gb300 import autotune
+
+    tp = autotune.tuned_params(len(pos), theta, kind) or {"n_leaf": 16, "n_crit": 64}
+    tc, acc, pot = _run(bh, pos, m, theta, eps, offsets=offsets, **tp, **kw)
+    t = oracle.build_tree(pos, m, tp["n_leaf"], tp["n_crit"], offsets=offsets)
     P.compare_tree(tc.tree(), t)
+    P.compare_moments(tc.moments(), t)
     groups = np.arange(0, t.G, every)
     acc_s, pot_s, st = oracle.walk(t, theta, eps, groups)
     gst = tc.group_stats()
-    sub = {k: v[groups] for k, v in gst.items()}
-    same = (sub["nc"] == st["nc"]) & (sub["np"] == st["np"]) & (sub["csum"] == st["csum"]) & (
-        sub["psum"] == st["psum"])
-    assert np.all(st["margin"][~same] < P.MARGIN)
-    bodies = np.concatenate([np.arange(t.gbeg[g], t.gend[g]) for g in groups[same]])
-    inp = t.perm[bodies]
-    an = np.linalg.norm(acc_s[bodies], axis=1)
-    scale = np.maximum(an, P.KAPPA * st["amag"][bodies])
-    rel = np.linalg.norm(acc[inp] - acc_s[bodies], axis=1) / scale
-    prel = np.abs(pot[inp] - pot_s[bodies]) / np.abs(pot_s[bodies])
-    assert rel.max() <= P.TOL and prel.max() <= P.TOL
-    return t, int((~same).sum())
+    rep = P.group_forces_report(acc, pot, t, groups, acc_s, pot_s, st, {k: v[groups] for k, v in gst.items()})
+    print(kind, tp, rep)
+    return t, rep
 
 
-def test_plummer_1m_sampled(cuda_lib):
-    """The benchmark's workload: 2^20-body Plummer sphere, theta = 0.5, eps = 0.005."""
+def test_plummer_1m_all_groups(cuda_lib):
+    """The benchmark's workload: 2^20-body Plummer sphere, theta = 0.5, eps =
+    0.005, every body compared."""
     pos, _, m = ics.plummer(1 << 20, 2)
-    _sampled_parity(cuda_lib, pos, m, 0.5, 0.005, every=400)
+    t, rep = _workload_parity(cuda_lib, pos, m, 0.5, 0.005, "plummer")
+    assert rep["bodies"] == 1 << 20
 
 
-def test_galaxy_8m_sampled(cuda_lib):
+def test_galaxy_8m(cuda_lib):
     """Hernquist sphere + exponential disk, 8,388,608 bodies: a sparse, very
-    non-uniform tree."""
+    non-uniform tree; every body compared."""
     pos, _, m = ics.galaxy(4194304, 4194304, 3)
-    t, flipped = _sampled_parity(cuda_lib, pos, m, 0.5, 0.01, every=3000, pool_per_body=512)
+    t, rep = _workload_parity(cuda_lib, pos, m, 0.5, 0.01, "galaxy")
     assert np.bincount(t.level).size > 12  # a deep tree
+    assert rep["bodies"] == len(pos)
 
 
-def test_ensemble_7m_sampled(cuda_lib):
-    """512 Plummer clusters of 1,024..65,536 bodies, ~7.7M bodies in one forest."""
+def test_ensemble_7m(cuda_lib):
+    """512 Plummer clusters of 1,024..65,536 bodies, ~7.7M bodies in one
+    forest; every body compared."""
     pos, _, m, off = ics.ensemble(512, 5)
-    t, flipped = _sampled_parity(cuda_lib, pos, m, 0.5, 0.01, every=3000, offsets=off, pool_per_body=512)
+    t, rep = _workload_parity(cuda_lib, pos, m, 0.5, 0.01, "ensemble", offsets=off)
     assert t.sys_root.min() >= 0
+    assert rep["bodies"] == len(pos)
 
 
 # ------------------------------------------------------- direct summation
