@@ -76,7 +76,10 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
     ap.add_argument("--key-levels", type=int, default=20,
                     help="key depth D (20: the paper's 60-bit keys; up to 30: 90-bit keys)")
-    ap.add_argument("--list-capacity", type=int, default=0, help="longest interaction list (0: library default)")
+    ap.add_argument("--list-capacity", type=int, default=0,
+                    help="split walk: longest interaction list (0: library default)")
+    ap.add_argument("--list-buffer", type=int, default=0,
+                    help="fused walk: entries of each list buffer of a walking warp (0: library default)")
     ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy", "nested"],
                     help="plummer: N-body Plummer sphere (--n); galaxy: Hernquist sphere + exponential disk, "
                          "8,388,608 bodies")
@@ -329,7 +332,7 @@ def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
     ctxs = []
     for s_ in range(n_sys):
         lo, hi = int(off[s_]), int(off[s_ + 1])
-        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048, list_capacity=4096)
+        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048, list_buffer=1024)
         tc.set_state(P[lo:hi], V[lo:hi], M[lo:hi])
         ctxs.append((lo, hi, tc))
     for _ in range(warmup):
@@ -453,6 +456,8 @@ def main():
     kw = dict(tuned or {}, walk_split=int(args.split), mac=args.mac, key_levels=args.key_levels)
     if args.list_capacity:
         kw["list_capacity"] = args.list_capacity
+    if args.list_buffer:
+        kw["list_buffer"] = args.list_buffer
     tc = bh.TreeCode(n, device=local, **kw)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
@@ -508,7 +513,8 @@ def main():
     achieved_walk = flops / walk_s if walk_s > 0 else 0.0
     # the committed counters are of the 1M Plummer step at theta = 0.5 with the default options
     profiled = (args.workload == "plummer" and args.n == N_BODIES and args.theta == THETA and args.mac == 0
-                and args.key_levels == 20 and not args.untuned and not args.list_capacity)
+                and args.key_levels == 20 and not args.untuned and not args.list_capacity
+                and not args.list_buffer)
     traffic = walk_traffic("eval_plummer_1m.md" if args.split else "walk_plummer_1m.md") if profiled else None
     clocks = clk.summary()
     mean_phase = {k: statistics.mean(p[k] for p in phases) for k in bh.PHASES if k != "call"}

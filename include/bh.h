@@ -40,8 +40,9 @@ typedef enum bh_status_code {
     BH_OK = 0,
     BH_ERR_INVALID_ARG = 1, /* bad pointer, size, parameter or offsets */
     BH_ERR_CAPACITY = 2,    /* n or n_sys above the context's maxima, or a walk
-                               stack, a group's list or the list pool overflowed
-                               (raise stack_capacity, list_capacity, pool_per_body) */
+                               stack, a group's list (split walk) or the list
+                               pool overflowed (raise stack_capacity,
+                               list_capacity, pool_per_body) */
     BH_ERR_NONFINITE = 3,   /* a position or mass is NaN or infinite */
     BH_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
     BH_ERR_CUDA = 5,        /* a CUDA runtime call failed */
@@ -64,8 +65,9 @@ typedef struct bh_params {
                                2: FP64 evaluation (a slow precision reference) */
     int32_t walk_warps;     /* warps per walk block: 4 (the walk kernels are compiled for it) */
     int32_t walk_blocks_per_sm; /* persistent grids = SMs x this; 0 = occupancy */
-    int32_t list_capacity;  /* longest cell list and longest particle list of one
-                               group (§2.2 interaction lists), default 16384 */
+    int32_t list_capacity;  /* split walk: longest cell list and longest particle
+                               list of one group (§2.2 interaction lists),
+                               default 16384 */
     int32_t pool_per_body;  /* interaction-list pool entries per body (the lists of
                                all groups of one walk, split walk only), default 768;
                                a pool above 2^34 entries (pool_per_body x n_max)
@@ -91,6 +93,11 @@ typedef struct bh_params {
                                ceil(3(D-20)/8) more digit passes and the workspace
                                24 B more per body.  Cells are identical to the 20-level
                                tree wherever no level-20 cell exceeds n_leaf. */
+    int32_t list_buffer;    /* fused walk: entries of each of a walking warp's two
+                               list buffers (cells, bodies), a multiple of 64 in
+                               128..2^20, default 4096.  A buffer is evaluated
+                               whenever it fills (§2.2, Fig. 3), so no list
+                               length is limited. */
 } bh_params;
 
 typedef struct bh_ctx bh_ctx; /* opaque, library-owned host object */

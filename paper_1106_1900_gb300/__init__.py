@@ -104,6 +104,7 @@ class bh_params(ctypes.Structure):
         ("walk_split", ctypes.c_int32),
         ("mac", ctypes.c_int32),
         ("key_levels", ctypes.c_int32),
+        ("list_buffer", ctypes.c_int32),
     ]
 
 

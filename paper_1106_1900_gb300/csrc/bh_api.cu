@@ -38,6 +38,7 @@ int validate_params(const bh_params *p) {
   if (p->walk_warps != 4) return BH_ERR_INVALID_ARG;  // the walk kernels are compiled for 4-warp blocks
   if (p->walk_blocks_per_sm < 0 || p->walk_blocks_per_sm > 64) return BH_ERR_INVALID_ARG;
   if (p->list_capacity < 64 || p->pool_per_body < 1) return BH_ERR_INVALID_ARG;
+  if (p->list_buffer < 128 || p->list_buffer > (1 << 20) || p->list_buffer % 64) return BH_ERR_INVALID_ARG;
   if (p->walk_split != 0 && p->walk_split != 1) return BH_ERR_INVALID_ARG;
   if (p->mac != 0 && p->mac != 1) return BH_ERR_INVALID_ARG;
   if (p->key_levels < bh::kLevels || p->key_levels > bh::kLevelsMax) return BH_ERR_INVALID_ARG;
@@ -88,7 +89,9 @@ int plan(Ctx &c, const bh_params *p, int64_t n_max, int32_t s_max, int device) {
   c.eval_grid = (int)std::min<int64_t>((int64_t)c.num_sms * eb, want);
   c.walk_grid = (int)std::min<int64_t>((int64_t)c.num_sms * fb, want);
   const bool fused = bh::walk_is_fused(*p);
-  c.trav_warps_total = (fused ? c.walk_grid : c.trav_grid) * bh::walk_block_warps();
+  // (a walk of the active groups of a block step is always fused, so the split
+  // form sizes its stacks and lists for both grids)
+  c.trav_warps_total = (fused ? c.walk_grid : std::max(c.trav_grid, c.walk_grid)) * bh::walk_block_warps();
   // the list pool serves the split walk only
   c.pool_cap = fused ? 32 : std::max<int64_t>((int64_t)p->pool_per_body * n_max, 1ll << 22);
   // group offsets into the pool are stored as 32-bit multiples of kPoolAlign
@@ -160,7 +163,9 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.scan_blocks = k.take<uint64_t>(std::max(R, N) / 4096 + 2);
   c.scan_total = k.take<uint64_t>(1);
   c.walk_stack = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.stack_capacity);
-  c.list_scratch = k.take<int32_t>((size_t)c.trav_warps_total * 2 * (size_t)c.p.list_capacity);
+  // the fused walk's bounded buffers, or the split walk's whole lists
+  c.list_scratch = k.take<int32_t>((size_t)c.trav_warps_total * (size_t)bh::walk_list_stride(c.p));
+  c.acc_hold = k.take<float4>(2 * N);
   c.list_pool = k.take<uint32_t>((size_t)c.pool_cap);
   c.pool_ctr = k.take<unsigned long long>(1);
   c.g_list = k.take<int4>(N);
@@ -334,6 +339,7 @@ int bh_default_params(bh_params *p) {
   p->walk_warps = 4;
   p->walk_blocks_per_sm = 0;
   p->list_capacity = 16384;
+  p->list_buffer = 4096;
   p->pool_per_body = 768;
   p->walk_split = 0;
   p->mac = 0;

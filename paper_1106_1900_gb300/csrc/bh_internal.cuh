@@ -115,7 +115,8 @@ struct Ctx {
   uint64_t *scan_total;          // [1]
   // walk
   int32_t *walk_stack;           // [traversal warps][2][stack_capacity]
-  int32_t *list_scratch;         // [traversal warps][2][list_capacity]
+  int32_t *list_scratch;         // [walking warps][2][list_buffer (fused) or list_capacity (split)]
+  float4 *acc_hold;              // [2 N] fused walk: per body (hi, lo) sums between evaluations of a list
   uint32_t *list_pool;           // [pool_cap] every group's cell list then particle list
   unsigned long long *pool_ctr;  // [1]
   int4 *g_list;                  // [G] {pool offset, cells, bodies, estimated evaluation cost}
@@ -166,6 +167,7 @@ enum OutMode { kOutCaller = 0, kOutSorted = 1 };
 cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s,
                         const uint8_t *g_active = nullptr);
 int walk_smem_bytes(int warps);
+int walk_list_stride(const bh_params &p);  // ints of list scratch per walking warp
 void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blocks_per_sm);
 // the fused walk unless the split form is asked for or the FP64 evaluation needs the pool
 inline bool walk_is_fused(const bh_params &p) { return p.walk_split == 0 && p.walk_variant != 2; }

@@ -1,21 +1,25 @@
 // k_walk.cu -- the breadth-first group walk and force evaluation (§2.2, §3.3).
 //
 // The paper walks and evaluates in one kernel: a group's interaction lists
-// fill shared memory and are evaluated whenever a tile is full.  Here one
-// warp does a group at a time, in two halves: traverse_group walks the tree
-// and writes the group's two lists to the warp's own scratch (global memory,
-// L2-resident), then eval_group sums them tile by tile.  The default kernel
-// runs both halves per group:
+// fill shared memory and are evaluated whenever they are full, the rest when
+// the walk ends.  Here one warp does a group at a time: walk_some walks the
+// tree, appending to two bounded list buffers of the warp (cells, bodies;
+// global memory, L2-resident), and eval_lists sums the buffered lists tile
+// by tile.  The default kernel runs both per group:
 //
 //  k_size_hist, k_order   place the groups by size, largest first (the cost
 //              of a group is not known before its walk).
-//  k_walk      persistent warps take groups from a counter in that order,
-//              walk each and evaluate its lists straight from the scratch:
-//              no list pool, and other warps' arithmetic runs while a warp
-//              walks.
+//  k_walk      persistent warps take groups from a counter in that order and
+//              walk each.  When the walk ends, the lists are evaluated
+//              straight from the buffers; when a buffer would overflow first
+//              (list_buffer entries), the walk pauses (its state saved in the
+//              warp's scratch), both buffers' whole tiles are evaluated, the
+//              rest moves to their fronts and the walk goes on.  No list
+//              length is limited, no list pool exists, and other warps'
+//              arithmetic runs while a warp walks.
 //
 // The split form (walk_split = 1; the FP64 evaluation variant always) runs
-// the halves as separate persistent kernels, bit-identical in result:
+// the two as separate persistent kernels on whole lists:
 //
 //  k_traverse  one warp per group (groups taken from a counter).  The current
 //              level of the walk is read 32 cells at a time from a per-warp
@@ -33,6 +37,8 @@
 //              ends on cheap groups.  Lists are summed 64 entries at a time:
 //              each lane gathers and stages two into shared memory, then every
 //              lane sums the tile from there.
+// The two forms build the same lists; with buffers at least as long as
+// every list they also sum them in the same order (identical results).
 //
 // Slots: every lane holds two target slots, 64 per warp.  A group of n <= 32
 // bodies is laid out with h = ceil(n/2): lane l holds bodies l mod h and
@@ -87,6 +93,13 @@ static_assert(kTile % 32 == 0 && kStage >= kTile + 6, "staging: whole warps per 
 // compensated (hi, lo) pair: 64 (32 measured 1.5 % slower; a plain FP32 sum
 // of 64 terms is off by ~sqrt(64) ulp of its terms' magnitude, typically).
 constexpr int kFoldEvery = 64;
+// Ints of list scratch per warp of the fused walk: a cell buffer and a body
+// buffer of cap entries each (cap a multiple of 64), then 32 waiting leaves
+// (int2), then the walk's state (kWalkStateInts; global memory, L1-cached:
+// shared memory is kept to what six blocks of the walk need per SM, which
+// leaves the L1 cache its size).
+constexpr int kWalkStateInts = 32;
+__host__ __device__ constexpr long walk_stride(int cap) { return 2L * cap + 64 + kWalkStateInts; }
 
 // Arithmetic variants: 0 group-relative FP32 with compensated tiles, 1 naive
 // FP32; 3 is variant 0 for keys deeper than 20 levels, whose cells can be
@@ -224,12 +237,12 @@ struct TravArgs {
   const int32_t *__restrict__ counts;
   int32_t *stack;
   int cap;
-  int32_t *scratch;  // [warps][2][list_cap]
-  int list_cap;
+  int32_t *scratch;  // per warp: list_cap cells, then list_cap bodies
+  int list_cap;      // entries of each list (fused walk: its buffers; split walk: a group's whole lists)
   uint32_t *pool;
   unsigned long long pool_cap;
   unsigned long long *pool_ctr;
-  int4 *g_list;  // per group: {pool offset, cells, bodies, estimated evaluation cost}
+  int4 *g_list;  // per group: {pool offset / kPoolAlign, cells, bodies, estimated evaluation cost}
   uint32_t *work_hist;  // groups per cost bucket
   int box_mac;           // 1: minimal-distance criterion (mac record = cube centre, half side)
   float two_over_theta;  // its l/theta = (l/2) (2/theta)
@@ -261,161 +274,250 @@ __device__ __forceinline__ void copy_list(uint32_t *__restrict__ dst, const int 
   }
 }
 
-// One group's walk (§2.2) by one warp: cell list to cl, particle list to pl
-// (the warp's scratch, list_cap entries each), level stacks cur/nxt.  Returns
-// the full list lengths (which may exceed list_cap: then only the first
-// list_cap entries are stored) and the warp-reduced index sums.
-struct Walked {
-  int ncell, npart;
-  unsigned long long csum, psum;
+// State of one group's breadth-first walk between two calls of walk_some: a
+// register copy in every lane of the warp (the same values), which the fused
+// walk saves to its scratch while it evaluates full buffers.
+struct __align__(16) WalkState {
+  float box[6];  // the group's tight bounding box (offsets from its centre c)
+  float c[3];    // the group's centre: its first body
+  int depth;     // levels of the walk so far
+  int ncur;      // cells of the current level (on the stack selected by flip)
+  int nnext;     // cells pushed for the next level
+  int base;      // next chunk of the current level
+  int flip;      // 0: the current level is on stack `cur`, 1: on `nxt`
+  int mid;       // 1: the walk stopped inside a level (at chunk `base`)
+  int bc;        // cells in the cell list (buffer)
+  int bp;        // bodies in the particle list (buffer)
+  int ncell;     // whole cell-list length
+  int npart;     // whole particle-list length (bodies)
+  int npend;     // opened leaves of the last chunk whose bodies are not all listed yet (in pend[])
+  int pend_tot;  // their bodies
+  int pend_done; // of which listed
+  int g;         // fused walk: the group (-1: none)
+  int parts;     // fused walk: evaluations of the group's buffers so far
+  unsigned long long csum, psum;  // sums of the listed cell and body indices
 };
 
+static_assert(sizeof(WalkState) <= 4 * kWalkStateInts, "the walk state fits its scratch slot");
+
+// Group g's walk starts: centre, tight bounding box, the root on stack cur.
 template <int VAR>
-__device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int lane, unsigned lt, int *cur, int *nxt,
-                                                 int *cl, int *pl) {
-  {
-    const int gb = A.g_beg[g];
-    const int n = A.g_beg[g + 1] - gb;
-    // group centre and tight bounding box (offsets from the centre, rounded)
-    float cx = 0.f, cy = 0.f, cz = 0.f;
-    if (relative(VAR)) {
-      const float4 c = A.part_hi[gb];
-      cx = c.x;
-      cy = c.y;
-      cz = c.z;
-    }
-    float bminx = INFINITY, bminy = INFINITY, bminz = INFINITY;
-    float bmaxx = -INFINITY, bmaxy = -INFINITY, bmaxz = -INFINITY;
-    for (int b = lane; b < n; b += 32) {
-      const Target t = make_target<VAR>(A.part_hi[gb + b], A.part_lo[gb + b], cx, cy, cz);
-      bminx = fminf(bminx, t.hx);
-      bminy = fminf(bminy, t.hy);
-      bminz = fminf(bminz, t.hz);
-      bmaxx = fmaxf(bmaxx, t.hx);
-      bmaxy = fmaxf(bmaxy, t.hy);
-      bmaxz = fmaxf(bmaxz, t.hz);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      bminx = fminf(bminx, __shfl_xor_sync(kFull, bminx, o));
-      bminy = fminf(bminy, __shfl_xor_sync(kFull, bminy, o));
-      bminz = fminf(bminz, __shfl_xor_sync(kFull, bminz, o));
-      bmaxx = fmaxf(bmaxx, __shfl_xor_sync(kFull, bmaxx, o));
-      bmaxy = fmaxf(bmaxy, __shfl_xor_sync(kFull, bmaxy, o));
-      bmaxz = fmaxf(bmaxz, __shfl_xor_sync(kFull, bmaxz, o));
-    }
-    int ncell = 0, npart = 0;
-    unsigned long long csum = 0, psum = 0;
-    // ---- breadth-first walk from the root of the group's system (§2.2)
-    if (lane == 0) cur[0] = A.sys_root[A.g_sys[g]];
-    __syncwarp();
-    int ncur = 1;
-    int *cstk = cur, *nstk = nxt;
-    int depth = 0;
-    while (ncur > 0) {
+__device__ __forceinline__ void walk_start(const TravArgs &A, WalkState &W, int g, int lane, int *cur) {
+  const int gb = A.g_beg[g];
+  const int n = A.g_beg[g + 1] - gb;
+  // group centre and tight bounding box (offsets from the centre, rounded)
+  float cx = 0.f, cy = 0.f, cz = 0.f;
+  if (relative(VAR)) {
+    const float4 c = A.part_hi[gb];
+    cx = c.x;
+    cy = c.y;
+    cz = c.z;
+  }
+  float bminx = INFINITY, bminy = INFINITY, bminz = INFINITY;
+  float bmaxx = -INFINITY, bmaxy = -INFINITY, bmaxz = -INFINITY;
+  for (int b = lane; b < n; b += 32) {
+    const Target t = make_target<VAR>(A.part_hi[gb + b], A.part_lo[gb + b], cx, cy, cz);
+    bminx = fminf(bminx, t.hx);
+    bminy = fminf(bminy, t.hy);
+    bminz = fminf(bminz, t.hz);
+    bmaxx = fmaxf(bmaxx, t.hx);
+    bmaxy = fmaxf(bmaxy, t.hy);
+    bmaxz = fmaxf(bmaxz, t.hz);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    bminx = fminf(bminx, __shfl_xor_sync(kFull, bminx, o));
+    bminy = fminf(bminy, __shfl_xor_sync(kFull, bminy, o));
+    bminz = fminf(bminz, __shfl_xor_sync(kFull, bminz, o));
+    bmaxx = fmaxf(bmaxx, __shfl_xor_sync(kFull, bmaxx, o));
+    bmaxy = fmaxf(bmaxy, __shfl_xor_sync(kFull, bmaxy, o));
+    bmaxz = fmaxf(bmaxz, __shfl_xor_sync(kFull, bmaxz, o));
+  }
+  // every lane holds the state (a register copy, uniform across the warp)
+  W.box[0] = bminx;
+  W.box[1] = bminy;
+  W.box[2] = bminz;
+  W.box[3] = bmaxx;
+  W.box[4] = bmaxy;
+  W.box[5] = bmaxz;
+  W.c[0] = cx;
+  W.c[1] = cy;
+  W.c[2] = cz;
+  W.depth = 0;
+  W.ncur = 1;
+  W.nnext = 0;
+  W.base = 0;
+  W.flip = 0;
+  W.mid = 0;
+  W.bc = W.bp = 0;
+  W.ncell = W.npart = 0;
+  W.npend = W.pend_tot = W.pend_done = 0;
+  W.csum = W.psum = 0ull;
+  if (lane == 0) cur[0] = A.sys_root[A.g_sys[g]];
+  __syncwarp();
+}
+
+// The bodies at positions done + lane of the opened leaves (first body of
+// leaf j = first_j, inclusive prefix of the counts = pin_j, held by lane j):
+// the leaf of each position is found by a binary search of the prefix sums
+// spread over the warp.  -1 past tot.
+__device__ __forceinline__ int leaf_body(int pin, int first, int pex, int done, int tot, int lane) {
+  const int si = done + lane;
+  int kk = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const int v = __shfl_sync(kFull, pin, kk + step - 1);
+    if (v <= si) kk += step;
+  }
+  const int of = __shfl_sync(kFull, first, kk);
+  const int oe = __shfl_sync(kFull, pex, kk);
+  return (si < tot) ? of + (si - oe) : -1;
+}
+
+// The breadth-first walk of §2.2 by one warp, from the state in W until it
+// ends (returns true) or, FUSED, until a buffer of list_cap entries is full
+// (returns false: the caller evaluates the buffers' whole tiles and calls
+// again).  Each lane applies the opening test (Eq. 1, or the
+// minimal-distance criterion) to one cell of a chunk of 32: accepted cells go
+// to the cell list cl, opened nodes push their (contiguous) children on the
+// next level's stack, opened leaves append their (contiguous) bodies to the
+// particle list pl; appends are warp ballots and prefix sums.  FUSED: a chunk
+// is started only if its accepted cells fit; the bodies of its opened leaves
+// go straight to the list if they fit, else the leaves wait (up to 32, right
+// after pl's cap entries, see list_waiting) and the walk stops.  Without
+// FUSED the lists are the group's whole lists: entries past list_cap are
+// counted but not stored.
+template <int VAR, bool FUSED>
+__device__ __forceinline__ bool walk_some(const TravArgs &A, WalkState &W, int lane, unsigned lt, int *cur, int *nxt,
+                                          int *cl, int *pl) {
+  const int cap = A.list_cap;
+  const float bminx = W.box[0], bminy = W.box[1], bminz = W.box[2];
+  const float bmaxx = W.box[3], bmaxy = W.box[4], bmaxz = W.box[5];
+  const float cx = W.c[0], cy = W.c[1], cz = W.c[2];
+  int depth = W.depth, ncur = W.ncur, nnext = W.nnext, base = W.base;
+  int bc = W.bc, bp = W.bp, ncell = W.ncell, npart = W.npart;
+  int flip = W.flip;
+  int *cstk = flip ? nxt : cur, *nstk = flip ? cur : nxt;
+  bool mid = W.mid != 0;  // resuming inside a level
+  // per-lane partial sums of the listed indices, lane 0 starting from the totals so far
+  unsigned long long csum = (lane == 0) ? W.csum : 0ull, psum = (lane == 0) ? W.psum : 0ull;
+  bool full = false;
+  while (!full && ncur > 0) {
+    if (!mid) {  // a new level
       if (++depth > kLevelsMax + 1) {  // a tree has at most D + 1 <= 31 levels: never loop on a corrupt one
         if (lane == 0) set_status(A.status, BH_ERR_STATE);
+        ncur = 0;
         break;
       }
-      int nnext = 0;
-      // the frontier is read 32 cells at a time; the next chunk's loads are
-      // issued before this chunk is processed (software pipelining)
-      int ci_n = 0;
-      float4 m_n = make_float4(0.f, 0.f, 0.f, 0.f);
-      int2 lk_n = make_int2(0, 0);
-      if (lane < ncur) {
-        ci_n = cstk[lane];
+      nnext = 0;
+      base = 0;
+    }
+    mid = false;
+    // the frontier is read 32 cells at a time; the next chunk's loads are
+    // issued before this chunk is processed (software pipelining)
+    int ci_n = 0;
+    float4 m_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    int2 lk_n = make_int2(0, 0);
+    if (base + lane < ncur) {
+      ci_n = cstk[base + lane];
+      m_n = A.mac[ci_n];
+      lk_n = A.link[ci_n];
+    }
+    int ci_nn = (base + 32 + lane < ncur) ? cstk[base + 32 + lane] : 0;  // stack entries run a chunk further ahead
+    for (; base < ncur; base += 32) {
+      if (FUSED && bc + 32 > cap) {  // this chunk's cells could overflow the buffer: evaluate first
+        full = true;
+        break;
+      }
+      const bool have = base + lane < ncur;
+      const int ci = ci_n;
+      const float4 m = m_n;
+      const int2 lk = lk_n;
+      if (base + 32 + lane < ncur) {
+        ci_n = ci_nn;
         m_n = A.mac[ci_n];
         lk_n = A.link[ci_n];
       }
-      int ci_nn = (32 + lane < ncur) ? cstk[32 + lane] : 0;  // stack entries run a chunk further ahead
-      for (int base = 0; base < ncur; base += 32) {
-        const bool have = base + lane < ncur;
-        const int ci = ci_n;
-        const float4 m = m_n;
-        const int2 lk = lk_n;
-        if (base + 32 + lane < ncur) {
-          ci_n = ci_nn;
-          m_n = A.mac[ci_n];
-          lk_n = A.link[ci_n];
+      if (base + 64 + lane < ncur) ci_nn = cstk[base + 64 + lane];
+      float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
+      if (VAR == kVarDeep && have) {  // cells below level 20 can be smaller than the float spacing at their position
+        const float4 ml = A.mac_lo[ci];
+        rx += ml.x;
+        ry += ml.y;
+        rz += ml.z;
+      }
+      float ex, ey, ez, ro;
+      if (!A.box_mac) {  // Eq. 1: the centre of mass's distance to the box against r_open = m.w
+        ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
+        ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy), 0.f);
+        ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz), 0.f);
+        ro = m.w;
+      } else {  // minimal distance: the gap between the cube (half side m.w) and the box against l/theta
+        ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx) - m.w, 0.f);
+        ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy) - m.w, 0.f);
+        ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz) - m.w, 0.f);
+        ro = m.w * A.two_over_theta;
+      }
+      const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      const bool accept = have && d2 > ro * ro;
+      const bool open = have && !accept;
+      const bool leaf = lk.y < 0;
+      // accepted cells -> cell list
+      const unsigned ab = __ballot_sync(kFull, accept);
+      if (accept) {
+        const int at = bc + __popc(ab & lt);
+        if (at < cap) cl[at] = ci;
+        csum += (unsigned long long)ci;
+      }
+      ncell += __popc(ab);
+      bc += __popc(ab);
+      // opened nodes -> children on the next level, opened leaves -> bodies
+      const int nch = (open && !leaf) ? min(max(lk.y, 0), 8) : 0;
+      const int np = (open && leaf) ? (lk.y & 0x7fffffff) : 0;
+      int inc, pin, tot, ptot;
+      if (__all_sync(kFull, np < (1 << 17))) {
+        // both prefix sums in one scan: children (<= 256 a chunk) in the low
+        // 10 bits, bodies (< 2^22 a chunk) above them
+        unsigned v = (unsigned)nch | ((unsigned)np << 10);
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(kFull, v, o);
+          if (lane >= o) v += y;
         }
-        if (base + 64 + lane < ncur) ci_nn = cstk[base + 64 + lane];
-        float rx = m.x - cx, ry = m.y - cy, rz = m.z - cz;
-        if (VAR == kVarDeep && have) {  // cells below level 20 can be smaller than the float spacing at their position
-          const float4 ml = A.mac_lo[ci];
-          rx += ml.x;
-          ry += ml.y;
-          rz += ml.z;
-        }
-        float ex, ey, ez, ro;
-        if (!A.box_mac) {  // Eq. 1: the centre of mass's distance to the box against r_open = m.w
-          ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx), 0.f);
-          ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy), 0.f);
-          ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz), 0.f);
-          ro = m.w;
-        } else {  // minimal distance: the gap between the cube (half side m.w) and the box against l/theta
-          ex = fmaxf(fmaxf(bminx - rx, rx - bmaxx) - m.w, 0.f);
-          ey = fmaxf(fmaxf(bminy - ry, ry - bmaxy) - m.w, 0.f);
-          ez = fmaxf(fmaxf(bminz - rz, rz - bmaxz) - m.w, 0.f);
-          ro = m.w * A.two_over_theta;
-        }
-        const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        const bool accept = have && d2 > ro * ro;
-        const bool open = have && !accept;
-        const bool leaf = lk.y < 0;
-        // accepted cells -> cell list
-        const unsigned ab = __ballot_sync(kFull, accept);
-        if (accept) {
-          const int at = ncell + __popc(ab & lt);
-          if (at < A.list_cap) cl[at] = ci;
-          csum += (unsigned long long)ci;
-        }
-        ncell += __popc(ab);
-        // opened nodes -> children on the next level, opened leaves -> bodies
-        const int nch = (open && !leaf) ? min(max(lk.y, 0), 8) : 0;
-        const int np = (open && leaf) ? (lk.y & 0x7fffffff) : 0;
-        int inc, pin, tot, ptot;
-        if (__all_sync(kFull, np < (1 << 17))) {
-          // both prefix sums in one scan: children (<= 256 a chunk) in the low
-          // 10 bits, bodies (< 2^22 a chunk) above them
-          unsigned v = (unsigned)nch | ((unsigned)np << 10);
-          for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(kFull, v, o);
-            if (lane >= o) v += y;
+        const unsigned vt = __shfl_sync(kFull, v, 31);
+        inc = (int)(v & 1023u);
+        pin = (int)(v >> 10);
+        tot = (int)(vt & 1023u);
+        ptot = (int)(vt >> 10);
+      } else {  // a leaf of 2^17 bodies or more (coincident positions): two scans
+        inc = nch;
+        pin = np;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, inc, o);
+          const int z = __shfl_up_sync(kFull, pin, o);
+          if (lane >= o) {
+            inc += y;
+            pin += z;
           }
-          const unsigned vt = __shfl_sync(kFull, v, 31);
-          inc = (int)(v & 1023u);
-          pin = (int)(v >> 10);
-          tot = (int)(vt & 1023u);
-          ptot = (int)(vt >> 10);
-        } else {  // a leaf of 2^17 bodies or more (coincident positions): two scans
-          inc = nch;
-          pin = np;
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, inc, o);
-            const int z = __shfl_up_sync(kFull, pin, o);
-            if (lane >= o) {
-              inc += y;
-              pin += z;
-            }
-          }
-          tot = __shfl_sync(kFull, inc, 31);
-          ptot = __shfl_sync(kFull, pin, 31);
         }
-        if (nnext + tot <= A.cap) {
-          int *dst = nstk + (nnext + inc - nch);
+        tot = __shfl_sync(kFull, inc, 31);
+        ptot = __shfl_sync(kFull, pin, 31);
+      }
+      if (nnext + tot <= A.cap) {
+        int *dst = nstk + (nnext + inc - nch);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)  // predicated stores, no divergent loop
-            if (j < nch) dst[j] = lk.x + j;
-          nnext += tot;
-        } else if (tot > 0) {
-          if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
-        }
-        // opened leaves -> their bodies on the particle list
-        if (ptot < 0 || ptot > A.n) {  // more bodies than exist: a corrupt link word
-          if (lane == 0) set_status(A.status, BH_ERR_STATE);
-          ptot = 0;
-        }
-        const int pex = pin - np;
+        for (int j = 0; j < 8; ++j)  // predicated stores, no divergent loop
+          if (j < nch) dst[j] = lk.x + j;
+        nnext += tot;
+      } else if (tot > 0) {
+        if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
+      }
+      // opened leaves -> their bodies on the particle list
+      if (ptot < 0 || ptot > A.n) {  // more bodies than exist: a corrupt link word
+        if (lane == 0) set_status(A.status, BH_ERR_STATE);
+        ptot = 0;
+      }
+      const int pex = pin - np;
+      npart += ptot;
+      if (!FUSED || bp + ptot <= cap) {
         for (int cb = 0; cb < ptot; cb += 32) {
           const int si = cb + lane;
           int kk = 0;
@@ -428,46 +530,109 @@ __device__ __forceinline__ Walked traverse_group(const TravArgs &A, int g, int l
           const int oe = __shfl_sync(kFull, pex, kk);
           if (si < ptot) {
             const int body = of + (si - oe);
-            const int at = npart + si;
-            if (at < A.list_cap) pl[at] = body;
+            const int at = bp + si;
+            if (at < cap) pl[at] = body;
             psum += (unsigned long long)body;
           }
         }
-        npart += ptot;
+        bp += ptot;
+      } else {  // not enough room: the leaves wait, their bodies are listed as the buffer empties
+        const unsigned lb = __ballot_sync(kFull, np > 0);
+        __syncwarp();
+        if (np > 0) reinterpret_cast<int2 *>(pl + cap)[__popc(lb & lt)] = make_int2(lk.x, np);
+        W.npend = __popc(lb);
+        W.pend_tot = ptot;
+        W.pend_done = 0;
+        __syncwarp();
+        full = true;  // the caller evaluates the buffers; the next call lists these bodies first
+        base += 32;   // this chunk is done (only bodies of its leaves wait)
+        break;
       }
-      __syncwarp();
-      int *t = cstk;
-      cstk = nstk;
-      nstk = t;
-      ncur = nnext;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      csum += __shfl_xor_sync(kFull, csum, o);
-      psum += __shfl_xor_sync(kFull, psum, o);
-    }
+    if (full) break;
     __syncwarp();
-    return Walked{ncell, npart, csum, psum};
+    int *t = cstk;
+    cstk = nstk;
+    nstk = t;
+    ncur = nnext;
+    flip ^= 1;
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    csum += __shfl_xor_sync(kFull, csum, o);
+    psum += __shfl_xor_sync(kFull, psum, o);
+  }
+  __syncwarp();
+  W.depth = depth;
+  W.ncur = ncur;
+  W.nnext = nnext;
+  W.base = base;
+  W.flip = flip;
+  W.mid = full;
+  W.bc = bc;
+  W.bp = bp;
+  W.ncell = ncell;
+  W.npart = npart;
+  W.csum = csum;
+  W.psum = psum;
+  return !full;
+}
+
+// The bodies of leaves waiting after pl's cap entries (W.npend leaves, their
+// W.pend_tot bodies, W.pend_done of them listed), appended to the particle
+// buffer 32 at a time while it has room; W is the walk's state saved in
+// memory (lane 0 updates it).  Returns true when all are listed.
+__device__ __forceinline__ bool list_waiting(WalkState &W, int *pl, int cap, int lane) {
+  const int npend = W.npend, tot = W.pend_tot;
+  int pd = W.pend_done, bp = W.bp;
+  const int2 pe = (lane < npend) ? reinterpret_cast<const int2 *>(pl + cap)[lane] : make_int2(0, 0);
+  int pin = pe.y;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, pin, o);
+    if (lane >= o) pin += y;
+  }
+  const int pex = pin - pe.y;
+  unsigned long long psum = 0;
+  while (pd < tot && bp + 32 <= cap) {
+    const int body = leaf_body(pin, pe.x, pex, pd, tot, lane);
+    if (body >= 0) {
+      pl[bp + lane] = body;
+      psum += (unsigned long long)body;
+    }
+    const int got = min(32, tot - pd);
+    bp += got;
+    pd += got;
+  }
+  for (int o = 16; o > 0; o >>= 1) psum += __shfl_xor_sync(kFull, psum, o);
+  __syncwarp();
+  if (lane == 0) {
+    W.pend_done = pd;
+    W.bp = bp;
+    W.psum += psum;
+  }
+  __syncwarp();
+  return pd >= tot;
 }
 
 // Per-group list statistics and the interaction counters (lane 0).
-__device__ __forceinline__ void record_group(const TravArgs &A, int g, int n, const Walked &w) {
-  A.g_npc[g] = w.ncell;
-  A.g_npp[g] = w.npart;
-  A.g_csum[g] = w.csum;
-  A.g_psum[g] = w.psum;
+__device__ __forceinline__ void record_group(const TravArgs &A, int g, int n, const WalkState &W) {
+  A.g_npc[g] = W.ncell;
+  A.g_npp[g] = W.npart;
+  A.g_csum[g] = W.csum;
+  A.g_psum[g] = W.psum;
   // every body of the group is on its own particle list once (its own
   // leaves are always opened for theta < 1.15): that self pair is not counted
-  const unsigned long long self = (w.npart >= n) ? (unsigned long long)n : 0ull;
-  atomicAdd(&A.totals[0], (unsigned long long)n * (unsigned long long)w.npart - self);
-  atomicAdd(&A.totals[1], (unsigned long long)n * (unsigned long long)w.ncell);
+  const unsigned long long self = (W.npart >= n) ? (unsigned long long)n : 0ull;
+  atomicAdd(&A.totals[0], (unsigned long long)n * (unsigned long long)W.npart - self);
+  atomicAdd(&A.totals[1], (unsigned long long)n * (unsigned long long)W.ncell);
 }
 
-// Split walk, first half: every group's lists into one pool at an exact
-// offset (one atomic per group), with an estimate of its evaluation cost.
+// Split walk, first half: every group's whole lists into one pool at an
+// exact offset (one atomic per group), with an estimate of its evaluation
+// cost.  A group's pool entry holds its cells, then its bodies.
 template <int VAR>
 __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
   const int lane = threadIdx.x & 31;
+  WalkState W;
   const size_t gw = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
   int *cur = A.stack + gw * 2 * (size_t)A.cap;
   int *nxt = cur + A.cap;
@@ -481,15 +646,16 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
     if (lane == 0) g = (int)atomicAdd(A.queue, 1u);
     g = __shfl_sync(kFull, g, 0);
     if (g >= G) break;
-    const Walked w = traverse_group<VAR>(A, g, lane, lt, cur, nxt, cl, pl);
+    walk_start<VAR>(A, W, g, lane, cur);
+    walk_some<VAR, false>(A, W, lane, lt, cur, nxt, cl, pl);
     bool full = false;
-    if (w.ncell > A.list_cap || w.npart > A.list_cap) {
+    if (W.ncell > A.list_cap || W.npart > A.list_cap) {
       full = true;
       if (lane == 0) set_status(A.status, BH_ERR_CAPACITY);
     }
     // ---- copy the lists into the pool at an exact offset, a multiple of
     // kPoolAlign entries so that offset / kPoolAlign fits the 32-bit field
-    const int nc = min(w.ncell, A.list_cap), npp = min(w.npart, A.list_cap);
+    const int nc = min(W.ncell, A.list_cap), npp = min(W.npart, A.list_cap);
     unsigned long long off = 0;
     if (lane == 0)
       off = atomicAdd(A.pool_ctr, (unsigned long long)((nc + npp + kPoolAlign - 1) / kPoolAlign * kPoolAlign));
@@ -511,7 +677,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(TravArgs A) {
       const int work = full ? 1 : P * ((2 * nc + npp + k - 1) / k + 1);
       A.g_list[g] = full ? make_int4(0, 0, 0, work) : make_int4((int)(unsigned)(off / kPoolAlign), nc, npp, work);
       atomicAdd(&A.work_hist[cost_bucket(work)], 1u);
-      record_group(A, g, n, w);
+      record_group(A, g, n, W);
     }
     __syncwarp();
   }
@@ -603,6 +769,7 @@ struct EvalArgs {
   float *acc_out;
   float *pot_out;
   const uint32_t *__restrict__ perm;
+  float4 *hold;  // [2 N] per body (sorted order): (hi, lo) sums between parts of a list (fused walk)
 };
 
 // The two target slots of a lane, as pairs (slot 0 in .x, slot 1 in .y).  The
@@ -737,11 +904,18 @@ __device__ __forceinline__ void init_stage(EvalSmem &S, int lane) {
   __syncwarp();
 }
 
-// Accelerations and potentials of group g's bodies from its cell list
-// clist[0..nc) and particle list plist[0..np), by one warp.
+// Accelerations and potentials of group g's bodies from (a part of) its cell
+// list clist[0..nc) and particle list plist[0..np), by one warp.
+//
+// The lists may come in parts (the fused walk evaluates its buffers whenever
+// they fill): `first` starts every body's sums at zero, `last` writes the
+// results.  Between parts a one-pass group keeps its slots' compensated sums
+// in shared memory; a group of several passes keeps, per body, the slots'
+// sums combined into one (hi, lo) pair in A.hold (sorted body order), and
+// restores it into the body's first slot.
 template <int VAR, bool GUARD, int MODE>
-__device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int lane, int g,
-                                           const uint32_t *clist, int nc, const uint32_t *plist, int np) {
+__device__ __forceinline__ void eval_lists(const EvalArgs &A, EvalSmem &S, int lane, int g, const uint32_t *clist,
+                                           int nc, const uint32_t *plist, int np, bool first, bool last) {
   const float2 e2 = f2(A.eps2, A.eps2);
   const float4 null_src = make_float4(kFar, kFar, kFar, 0.f);  // far away, zero mass, no quadrupole
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -766,6 +940,9 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
     const int ph = min(lane / h, k - 1);
     const int b0 = lane % h, b1 = b0 + h;
     const bool v0 = lane < h * k && b0 < n, v1 = lane < h * k && b1 < n;
+    // body b's first slot: b (k = 1: b < 32) or 32 + b - 32 (k = 1: b >= 32);
+    // for k > 1, b for b < h and 32 + b - h otherwise
+    const int s0 = (lane < h) ? lane : 32 + lane - h;
     Targets2 T;
     {
       const int lb0 = gb + min(b0, n - 1), lb1 = gb + min(b1, n - 1);
@@ -778,10 +955,28 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
       T.nly = f2(-t0.ly, -t1.ly);
       T.nlz = f2(-t0.lz, -t1.lz);
     }
-    S.ah[lane] = zero4;
-    S.al[lane] = zero4;
-    S.ah[32 + lane] = zero4;
-    S.al[32 + lane] = zero4;
+    if (first || npass > 1) {
+      S.ah[lane] = zero4;
+      S.al[lane] = zero4;
+      S.ah[32 + lane] = zero4;
+      S.al[32 + lane] = zero4;
+      if (!first) {  // several passes: this pass's sums so far, one pair per body, into its first slot
+        __syncwarp();
+        if (k == 1) {
+          if (v0) {
+            S.ah[lane] = A.hold[2 * (gb + b0)];
+            S.al[lane] = A.hold[2 * (gb + b0) + 1];
+          }
+          if (v1) {
+            S.ah[32 + lane] = A.hold[2 * (gb + b1)];
+            S.al[32 + lane] = A.hold[2 * (gb + b1) + 1];
+          }
+        } else if (lane < n) {
+          S.ah[s0] = A.hold[2 * (gb + lane)];
+          S.al[s0] = A.hold[2 * (gb + lane) + 1];
+        }
+      }
+    }
     Acc2 t;  // partial sums since the last fold
     t.x = t.y = t.z = t.np = f2(0.f, 0.f);
     int since = 0;  // interactions per slot since the last fold
@@ -879,45 +1074,44 @@ __device__ __forceinline__ void eval_group(const EvalArgs &A, EvalSmem &S, int l
     fold2<VAR>(S, lane, t);
     __syncwarp();
 
-    // ---- combine the slots of each body and write
-    auto write_body = [&](int b, float ox, float oy, float oz, float op) {
+    // ---- combine the slots of each body: write the results, or (several
+    // passes, more parts to come) keep the pair
+    auto put_body = [&](int b, const float4 &H, const float4 &Lo) {
       const int gi = gb + b;
-      if (MODE == kOutSorted) {
-        A.acc_sorted[gi] = make_float4(ox, oy, oz, op);
+      if (!last) {
+        A.hold[2 * gi] = H;
+        A.hold[2 * gi + 1] = Lo;
+      } else if (MODE == kOutSorted) {
+        A.acc_sorted[gi] = make_float4(H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
       } else {
         const size_t j = A.perm[gi];
-        A.acc_out[3 * j] = ox;
-        A.acc_out[3 * j + 1] = oy;
-        A.acc_out[3 * j + 2] = oz;
-        A.pot_out[j] = op;
+        A.acc_out[3 * j] = H.x + Lo.x;
+        A.acc_out[3 * j + 1] = H.y + Lo.y;
+        A.acc_out[3 * j + 2] = H.z + Lo.z;
+        A.pot_out[j] = H.w + Lo.w;
       }
     };
-    if (k == 1) {
-      if (v0) {
-        const float4 H = S.ah[lane], Lo = S.al[lane];
-        write_body(b0, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
+    if (last || npass > 1) {
+      if (k == 1) {
+        if (v0) put_body(b0, S.ah[lane], S.al[lane]);
+        if (v1) put_body(b1, S.ah[32 + lane], S.al[32 + lane]);
+      } else if (lane < n) {
+        // body b's slots: b + q h (q < k) in the first half of the slot array
+        // for b < h, b - h + q h in the second half otherwise
+        float4 H = S.ah[s0], Lo = S.al[s0];
+        for (int q = 1; q < k; ++q) {
+          const float4 hq = S.ah[s0 + q * h], lq = S.al[s0 + q * h];
+          two_sum_into(H.x, Lo.x, hq.x);
+          two_sum_into(H.y, Lo.y, hq.y);
+          two_sum_into(H.z, Lo.z, hq.z);
+          two_sum_into(H.w, Lo.w, hq.w);
+          Lo.x += lq.x;
+          Lo.y += lq.y;
+          Lo.z += lq.z;
+          Lo.w += lq.w;
+        }
+        put_body(lane, H, Lo);
       }
-      if (v1) {
-        const float4 H = S.ah[32 + lane], Lo = S.al[32 + lane];
-        write_body(b1, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
-      }
-    } else if (lane < n) {
-      // body b's slots: b + q h (q < k) in the first half of the slot array
-      // for b < h, b - h + q h in the second half otherwise
-      const int s0 = (lane < h) ? lane : 32 + lane - h;
-      float4 H = S.ah[s0], Lo = S.al[s0];
-      for (int q = 1; q < k; ++q) {
-        const float4 hq = S.ah[s0 + q * h], lq = S.al[s0 + q * h];
-        two_sum_into(H.x, Lo.x, hq.x);
-        two_sum_into(H.y, Lo.y, hq.y);
-        two_sum_into(H.z, Lo.z, hq.z);
-        two_sum_into(H.w, Lo.w, hq.w);
-        Lo.x += lq.x;
-        Lo.y += lq.y;
-        Lo.z += lq.z;
-        Lo.w += lq.w;
-      }
-      write_body(lane, H.x + Lo.x, H.y + Lo.y, H.z + Lo.z, H.w + Lo.w);
     }
     __syncwarp();
   }  // passes
@@ -939,31 +1133,38 @@ __global__ void __launch_bounds__(kThreads, kEvalMinBlocks) k_eval(EvalArgs A) {
     if (q >= NQ) break;
     const int g = A.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
-    const int4 L = A.g_list[g];
+    const int4 L = A.g_list[g];  // {offset / kPoolAlign, cells, bodies, cost}: cells, then bodies
     const uint32_t *lst = A.pool + (size_t)kPoolAlign * (unsigned)L.x;
     // pull the group's lists from DRAM into L2 now (one 128-byte line per 32 entries)
     for (int i = 32 * lane; i < L.y + L.z; i += 32 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(lst + i));
-    eval_group<VAR, GUARD, MODE>(A, S, lane, g, lst, L.y, lst + L.y, L.z);
+    eval_lists<VAR, GUARD, MODE>(A, S, lane, g, lst, L.y, lst + L.y, L.z, true, true);
   }
 }
 
-// Fused walk: a warp walks a group into its own list scratch and evaluates
-// it from there at once, the next group's walk overlapping other warps'
-// evaluations on the same SM (the walk is issue- and latency-bound on the
-// integer and load pipes, the evaluation bound by the FP32 pipe).  No list
-// pool, no copy; groups are taken largest first.
+// Fused walk: a warp alternates between walking its group (walk_some, the
+// walk's state kept in shared memory) and evaluating the group's list
+// buffers: whenever a buffer of list_buffer entries fills, the whole tiles
+// of both buffers are evaluated and the rest moves to their fronts; when the
+// walk ends, everything left (§2.2, Fig. 3: lists are evaluated as they
+// fill, the remainder at the end).  The buffers (per warp: list_buffer cells
+// and as many bodies) stay in L2, and no list length is limited.  Walk and
+// evaluation are each inlined once, so each has the kernel's registers to
+// itself.  Groups are taken largest first; one warp's walk overlaps other
+// warps' evaluations on the SM (the walk is issue- and latency-bound on the
+// integer and load pipes, the evaluation bound by the FP32 pipe).
 template <int VAR, bool GUARD, int MODE>
 __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(TravArgs T, EvalArgs E) {
   extern __shared__ EvalSmem s_eval[];
   const int lane = threadIdx.x & 31;
   EvalSmem &S = s_eval[threadIdx.x >> 5];
   init_stage(S, lane);
-  const size_t gw = (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  int *cur = T.stack + gw * 2 * (size_t)T.cap;
-  int *nxt = cur + T.cap;
-  int *cl = T.scratch + gw * 2 * (size_t)T.list_cap;
-  int *pl = cl + T.list_cap;
-  const unsigned lt = lanemask_lt();
+  // this warp's stacks and buffers (recomputed where used: fewer live registers)
+  auto gw = [&]() { return (size_t)blockIdx.x * kWarps + (threadIdx.x >> 5); };
+  auto stk = [&]() { return T.stack + gw() * 2 * (size_t)T.cap; };
+  auto cls = [&]() { return T.scratch + gw() * (size_t)walk_stride(T.list_cap); };  // cells, bodies, waiting leaves
+  auto saved = [&]() -> WalkState & {
+    return *reinterpret_cast<WalkState *>(cls() + 2 * (size_t)T.list_cap + 64);
+  };
   const int G = T.counts[1], NQ = T.counts[3];  // groups; groups in the order (the active ones)
   while (true) {
     int q = 0;
@@ -972,15 +1173,56 @@ __global__ void __launch_bounds__(kThreads, kWalkMinBlocks) k_walk(TravArgs T, E
     if (q >= NQ) break;
     const int g = E.order[q];
     if ((unsigned)g >= (unsigned)G) continue;  // (never: k_order fills every slot)
-    const Walked w = traverse_group<VAR>(T, g, lane, lt, cur, nxt, cl, pl);
-    const bool full = w.ncell > T.list_cap || w.npart > T.list_cap;
-    if (lane == 0) {
-      if (full) set_status(T.status, BH_ERR_CAPACITY);
-      record_group(T, g, T.g_beg[g + 1] - T.g_beg[g], w);
+    WalkState W;  // the walk's state, in registers while the warp walks
+    walk_start<VAR>(T, W, g, lane, stk());
+    for (int parts = 0;; ++parts) {
+      const bool done = walk_some<VAR, true>(T, W, lane, lanemask_lt(), stk(), stk() + T.cap, cls(),
+                                             cls() + T.list_cap);
+      int wc = W.bc, wp = W.bp;  // everything at the walk's end
+      if (done) {
+        if (lane == 0) record_group(T, g, T.g_beg[g + 1] - T.g_beg[g], W);
+      } else {  // whole tiles now; the state waits in the scratch meanwhile
+        wc &= ~(kTile - 1);
+        wp &= ~(kTile - 1);
+        if (lane == 0) saved() = W;
+      }
+      __syncwarp();
+      const uint32_t *c = reinterpret_cast<const uint32_t *>(cls());
+      if (parts == 0 && done)  // the common case: the whole lists in one evaluation
+        eval_lists<VAR, GUARD, MODE>(E, S, lane, g, c, wc, c + T.list_cap, wp, true, true);
+      else
+        eval_lists<VAR, GUARD, MODE>(E, S, lane, g, c, wc, c + T.list_cap, wp, parts == 0, done);
+      if (done) break;
+      // the rest of each buffer (fewer than kTile entries) to its front, then
+      // the bodies of waiting leaves, evaluating the particle buffer whenever
+      // it fills
+      WalkState &M = saved();
+      int *cl = cls(), *pl = cl + T.list_cap;
+      while (true) {
+        const int bc = M.bc, bp = M.bp;
+        const int mc = bc & ~(kTile - 1), mp = bp & ~(kTile - 1);
+        const int rc = bc - mc, rp = bp - mp;
+        int c0 = 0, c1 = 0, p0 = 0, p1 = 0;
+        if (lane < rc) c0 = cl[mc + lane];
+        if (32 + lane < rc) c1 = cl[mc + 32 + lane];
+        if (lane < rp) p0 = pl[mp + lane];
+        if (32 + lane < rp) p1 = pl[mp + 32 + lane];
+        __syncwarp();
+        if (lane < rc) cl[lane] = c0;
+        if (32 + lane < rc) cl[32 + lane] = c1;
+        if (lane < rp) pl[lane] = p0;
+        if (32 + lane < rp) pl[32 + lane] = p1;
+        if (lane == 0) {
+          M.bc = rc;
+          M.bp = rp;
+        }
+        __syncwarp();
+        if (M.pend_done >= M.pend_tot || list_waiting(M, pl, T.list_cap, lane)) break;
+        ++parts;  // the particle buffer is full again: its whole tiles
+        eval_lists<VAR, GUARD, MODE>(E, S, lane, g, c, 0, c + T.list_cap, M.bp & ~(kTile - 1), false, false);
+      }
+      W = M;
     }
-    __syncwarp();  // the lists written by every lane are visible to every lane
-    eval_group<VAR, GUARD, MODE>(E, S, lane, g, reinterpret_cast<const uint32_t *>(cl), full ? 0 : w.ncell,
-                                 reinterpret_cast<const uint32_t *>(pl), full ? 0 : w.npart);
   }
 }
 
@@ -1001,7 +1243,7 @@ __global__ void __launch_bounds__(kThreads) k_eval_f64(EvalArgs A) {
     if (g >= G) break;
     const int gb = A.g_beg[g];
     const int n = A.g_beg[g + 1] - gb;
-    const int4 L = A.g_list[g];
+    const int4 L = A.g_list[g];  // cells, then bodies
     const uint32_t *clist = A.pool + (size_t)kPoolAlign * (unsigned)L.x;
     const uint32_t *plist = clist + L.y;
     for (int b = lane; b < n; b += 32) {  // (one sweep: this study variant is not tuned)
@@ -1072,6 +1314,14 @@ cudaError_t launch_fused(Ctx &c, const TravArgs &t, const EvalArgs &a, cudaStrea
 
 int walk_smem_bytes(int warps) { return warps * (int)sizeof(EvalSmem); }
 
+// Ints of list scratch per walking warp: the fused walk's buffers, or for
+// the split walk two lists of list_capacity entries (or the buffers if
+// larger: a walk restricted to active groups is always fused).
+int walk_list_stride(const bh_params &p) {
+  const long fused = walk_stride(p.list_buffer), split = 2L * p.list_capacity;
+  return (int)((walk_is_fused(p) || fused > split) ? fused : split);
+}
+
 cudaError_t walk_init_attrs(int smem) {
   cudaError_t e = cudaSuccess;
 #define BH_EVAL_ATTR(V, G, M)                                                                        \
@@ -1127,7 +1377,8 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   t.stack = c.walk_stack;
   t.cap = c.p.stack_capacity;
   t.scratch = c.list_scratch;
-  t.list_cap = c.p.list_capacity;
+  // the fused walk's bounded buffers, or the split walk's whole lists
+  t.list_cap = (walk_is_fused(c.p) || g_active) ? c.p.list_buffer : c.p.list_capacity;
   t.pool = c.list_pool;
   t.pool_cap = (unsigned long long)c.pool_cap;
   t.pool_ctr = c.pool_ctr;
@@ -1158,6 +1409,7 @@ cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc
   a.acc_out = acc;
   a.pot_out = pot;
   a.perm = c.idx[0];
+  a.hold = c.acc_hold;
   // keys deeper than 20 levels take the deep form of variant 0 (and of the FP64 variant's walk)
   const bool deep = c.levels > kLevels;
   const int var = (c.p.walk_variant == 0 && deep) ? kVarDeep : c.p.walk_variant;

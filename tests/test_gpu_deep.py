@@ -37,6 +37,17 @@ def test_deep_keys_nested_cluster(cuda_lib, D):
     assert t.level.max() > 20
 
 
+def test_crowded_level20_leaf_small_buffers(cuda_lib):
+    # with 20-level keys most of the 3000-body cluster is one level-20 leaf
+    # (2,839 bodies): every group near it opens that leaf, whose bodies pass
+    # through a 128-entry particle buffer in parts (no list length limit)
+    pos, _, m = ics.nested(20001, 5, 3000)
+    tc, t, rep = _deep_parity(cuda_lib, pos, m, 0.5, 1e-7, 20, list_buffer=128)
+    leaf = t.is_leaf == 1
+    assert (t.pend[leaf] - t.pbeg[leaf]).max() > 2000  # one crowded level-20 leaf
+    assert tc.group_stats()["np"].max() > 2000
+
+
 def test_deep_keys_equal_20_levels_when_uncrowded(cuda_lib):
     # no level-20 cell holds more than N_leaf bodies: the same tree and moments
     # bit for bit; the walks differ in rounding (30-level keys round each

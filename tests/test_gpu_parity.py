@@ -329,7 +329,8 @@ def test_fused_walk_equals_split_walk(cuda_lib, variant, n_crit):
     P, M = torch.from_numpy(pos).cuda(), torch.from_numpy(m).cuda()
     out = []
     for split in (0, 1):
-        tc = cuda_lib.TreeCode(len(pos), walk_split=split, walk_variant=variant, n_crit=n_crit)
+        # a list buffer longer than every list: the fused walk evaluates each list once, at its end
+        tc = cuda_lib.TreeCode(len(pos), walk_split=split, walk_variant=variant, n_crit=n_crit, list_buffer=16384)
         tc.build(P, M)
         acc, pot = tc.compute_forces(0.5, 0.01)
         tc.check()
@@ -339,6 +340,34 @@ def test_fused_walk_equals_split_walk(cuda_lib, variant, n_crit):
     for k in ("nc", "np", "csum", "psum"):
         assert np.array_equal(g0[k], g1[k])
     assert (c0["pp"], c0["pc"]) == (c1["pp"], c1["pc"])
+
+
+@pytest.mark.parametrize("n_leaf,n_crit,theta", [(8, 64, 0.5), (8, 128, 0.5), (16, 256, 0.3), (4, 40, 0.75)])
+def test_small_list_buffers(cuda_lib, n_leaf, n_crit, theta):
+    """§2.2, Fig. 3: the fused walk evaluates a list buffer whenever it fills
+    and the rest at the end.  With 128-entry buffers every long list is
+    evaluated in many parts (one-pass groups keep their sums in shared
+    memory between parts, several-pass groups per body in the workspace):
+    the results meet the same tolerance against the oracle."""
+    pos, _, m = ics.plummer(16384, 1)
+    tc, t, rep = _full_parity(cuda_lib, pos, m, theta, 0.01, n_leaf, n_crit, list_buffer=128)
+    st = tc.group_stats()
+    assert st["nc"].max() > 8 * 128 and st["np"].max() > 2 * 128  # lists many buffers long
+
+
+def test_small_list_buffers_forest_and_split(cuda_lib):
+    pos, _, m, off = ics.ensemble(n_sys=30, seed=19, n_min=1, n_max=4000)
+    _full_parity(cuda_lib, pos, m, 0.4, 0.01, offsets=off, list_buffer=192)
+    # 1024-entry buffers against whole lists (split walk): same lists, equal within the tolerance
+    pos, _, m = ics.plummer(30000, 4)
+    tc, acc, pot = _run(cuda_lib, pos, m, 0.3, 0.005, 8, 128, list_buffer=1024)
+    tc2, acc2, pot2 = _run(cuda_lib, pos, m, 0.3, 0.005, 8, 128, walk_split=1)
+    g, g2 = tc.group_stats(), tc2.group_stats()
+    for k in ("nc", "np", "csum", "psum"):
+        assert np.array_equal(g[k], g2[k])
+    assert g["nc"].max() > 1024  # the buffers were evaluated in parts
+    scale = np.linalg.norm(acc2, axis=1)
+    assert np.max(np.linalg.norm(acc - acc2, axis=1) / scale) < 2e-6
 
 
 @pytest.mark.parametrize("theta,split", [(0.5, 0), (0.75, 0), (0.5, 1)])
