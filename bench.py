@@ -74,6 +74,11 @@ def parse():
     ap.add_argument("--split", action="store_true",
                     help="split walk (lists through a pool, then a separate evaluation kernel)")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-vs-plain ensemble comparison")
+    ap.add_argument("--shard", action="store_true",
+                    help="one system with its groups shared out among the ranks (strong scaling) instead of "
+                         "an independent system per rank")
+    ap.add_argument("--ensemble-steps", type=int, default=100,
+                    help="steps of each arm of the batched-vs-plain ensemble comparison")
     ap.add_argument("--key-levels", type=int, default=20,
                     help="key depth D (20: the paper's 60-bit keys; up to 30: 90-bit keys)")
     ap.add_argument("--list-capacity", type=int, default=0,
@@ -296,12 +301,18 @@ def block_compare(bh, dev, pos, vel, mass, theta, eps, params, dt_max=1.0 / 64, 
             "speedup_vs_shared": shared_interval_s / wall}
 
 
-def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
+def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512, params=None):
     """512 independent Plummer clusters (sizes log-uniform in [1024, 65536],
     scale radii U(0.5, 2)): one forest stepped as one CUDA graph per step
-    against one context per cluster, each stepping its own graph.  Both arms
-    compute identical forces (a forest's systems share nothing), so the
-    error is equal by construction; the final states are compared."""
+    against one context per cluster, each stepping its own graph, all from
+    the same initial state.
+
+    The plain arm runs the paper's N_leaf = 16, N_crit = 64.  The batched arm
+    runs (a) the autotuner's parameters for this workload (`params`), whose
+    99th-percentile force error is no larger than the paper pair's times
+    1.05 (the autotuner's rule), and (b) the paper pair itself: the same
+    trees, lists and forces as the plain arm (a forest's systems share
+    nothing), so the two end in the same states, which is checked."""
     import numpy as np
     import torch
 
@@ -311,28 +322,34 @@ def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
     N = len(pos)
     P, V, M = (torch.from_numpy(a).to(dev) for a in (pos, vel, m))
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    # batched: one forest, one graph per step
-    tf = bh.TreeCode(N, n_sys, device=dev.index)
-    tf.set_state(P, V, M, offsets=off)
-    for _ in range(warmup):
-        tf.step(DT, theta, eps, graph=True)
-    torch.cuda.synchronize()
-    a, b = ev(), ev()
-    a.record()
-    for _ in range(steps):
-        tf.step(DT, theta, eps, graph=True)
-    b.record()
-    torch.cuda.synchronize()
-    tf.check()
-    t_batched = a.elapsed_time(b) * 1e-3
-    xf = torch.empty_like(P)
-    tf.get_state(xf)
-    tf.close()
+    paper = {"n_leaf": 16, "n_crit": 64}
+
+    def batched(prm):
+        # one forest, one graph per step
+        tf = bh.TreeCode(N, n_sys, device=dev.index, **prm)
+        tf.set_state(P, V, M, offsets=off)
+        for _ in range(warmup):
+            tf.step(DT, theta, eps, graph=True)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(steps):
+            tf.step(DT, theta, eps, graph=True)
+        b.record()
+        torch.cuda.synchronize()
+        tf.check()
+        xf = torch.empty_like(P)
+        tf.get_state(xf)
+        tf.close()
+        return a.elapsed_time(b) * 1e-3, xf
+
+    t_tuned, _ = batched(dict(params or paper))
+    t_batched, xf = batched(paper)
     # plain: one context and graph per system, launched one after another
     ctxs = []
     for s_ in range(n_sys):
         lo, hi = int(off[s_]), int(off[s_ + 1])
-        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048, list_buffer=1024)
+        tc = bh.TreeCode(hi - lo, device=dev.index, stack_capacity=2048, **paper)
         tc.set_state(P[lo:hi], V[lo:hi], M[lo:hi])
         ctxs.append((lo, hi, tc))
     for _ in range(warmup):
@@ -356,10 +373,14 @@ def ensemble_compare(bh, dev, theta, eps, steps, warmup, n_sys=512):
         tc.close()
     return {"workload": f"{n_sys} Plummer clusters, N={N} (sizes log-uniform 1024..65536, seeds 5000+s), "
                         f"theta={theta}, eps={eps}, dt=1/64",
-            "steps": steps, "batched_particles_per_s": N * steps / t_batched,
-            "plain_particles_per_s": N * steps / t_plain, "speedup": t_plain / t_batched,
-            "batched_ms_per_step": 1e3 * t_batched / steps, "plain_ms_per_step": 1e3 * t_plain / steps,
-            "max_state_difference": maxdiff}
+            "steps": steps,
+            "batched_params": params or paper, "batched_particles_per_s": N * steps / t_tuned,
+            "batched_ms_per_step": 1e3 * t_tuned / steps,
+            "plain_params": paper, "plain_particles_per_s": N * steps / t_plain,
+            "plain_ms_per_step": 1e3 * t_plain / steps,
+            "speedup": t_plain / t_tuned,
+            "same_params": {"params": paper, "batched_particles_per_s": N * steps / t_batched,
+                            "speedup": t_plain / t_batched, "max_state_difference": maxdiff}}
 
 
 def run_reference(args):
@@ -414,10 +435,77 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_sharded(args):
+    """One system shared out among the ranks (paper_1106_1900_gb300.shard):
+    every rank builds the same tree, walks its range of groups, and one
+    all-gather per step exchanges the walked bodies' forces (strong scaling:
+    the same bodies whatever the number of ranks)."""
+    import torch
+
+    import ics
+    import paper_1106_1900_gb300 as bh
+    from paper_1106_1900_gb300 import autotune, shard
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bh.load()
+    pos, vel, m = ics.plummer(args.n, SEED)  # the same system on every rank
+    n = len(pos)
+    tuned = None if args.untuned else autotune.tuned_params(n, args.theta, "plummer")
+    tc = bh.TreeCode(n, device=local, **(tuned or {}))
+    tc.set_state(*(torch.from_numpy(a).to(dev) for a in (pos, vel, m)))
+    st = shard.ShardedStep(tc, rank, world)
+    flush = torch.empty(max(args.flush_mb, 1) << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        st.step(DT, args.theta, EPS)
+    tc.check()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total = 0.0
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            if args.flush_mb > 0:
+                flush.fill_(k & 0xff)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st.step(DT, args.theta, EPS)
+            b.record()
+            torch.cuda.synchronize()
+            total += a.elapsed_time(b)
+    if world > 1:
+        torch.distributed.barrier()
+    tc.check()
+    t_max = max_over_ranks(total, world, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": n * args.steps / (t_max * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"Plummer N={n} (seed {SEED}), theta={args.theta}, eps={EPS}, dt=1/64, one system",
+                       "global_batch": n, "parallelism": f"groups shared out over {world} ranks, tree on every rank",
+                       "exchange": "one all-gather of the walked bodies' forces (16 B per body) and one of the "
+                                   "groups' interaction counts per step",
+                       "l2": f"flushed between timed steps ({args.flush_mb} MB write)" if args.flush_mb else "not flushed",
+                       "params": tuned or "library defaults", "last_split": st.last_ranges},
+            "clocks": clk.summary(),
+        }), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.shard:
+        run_sharded(args)
         return
     import numpy as np
     import torch
@@ -550,7 +638,8 @@ def main():
         tc2.close()
     ens = None
     if not args.no_ensemble and args.workload == "plummer":
-        ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=3, warmup=2)
+        ens_params = None if args.untuned else autotune.tuned_params(7672972, args.theta, "ensemble")
+        ens = ensemble_compare(bh, dev, args.theta, 0.01, steps=args.ensemble_steps, warmup=3, params=ens_params)
     blk = None
     if args.block:
         blk = {"rebuild_every_step": block_compare(bh, dev, P, V, M, args.theta, eps, kw, eta=args.block_eta,

@@ -210,6 +210,37 @@ int bh_block_info(bh_ctx *ctx, int64_t out[4], void *stream);
  * device buffers in the caller's order; either may be NULL. */
 int bh_block_levels(bh_ctx *ctx, int32_t *level_dev, int64_t *tick_dev, void *stream);
 
+/* A leapfrog step in three parts, for a system whose groups are shared out
+ * among several GPUs (the paper's §5 names splitting the work over GPUs as
+ * the way to larger systems; here the tree is built on every GPU and the
+ * groups are split): every rank holds the whole state, builds the same tree,
+ * walks only its own contiguous range of groups, exchanges the accelerations
+ * of its groups' bodies with the other ranks (the caller's collective, e.g.
+ * an all-gather over NCCL), and then corrects every body, so that all ranks
+ * hold the same state again.
+ *
+ * bh_step_begin: the predictor (skipped with init = 1: the initial force
+ *   evaluation at the loaded state, which must come first, once) and the
+ *   build at the predicted positions.  Stream-ordered.
+ * bh_walk_groups: the walk (§2.2) of groups g_begin <= g < g_end of that
+ *   build (group order: bh_get_tree's gbeg), writing the accelerations and
+ *   potentials of their bodies (sorted body range gbeg[g_begin] ..
+ *   gend[g_end - 1]) into the context's sorted force array; may be called
+ *   for several ranges.  g_end past the last group is clamped.  The walked
+ *   groups' list statistics (bh_get_group_stats) are this walk's; the other
+ *   groups' are left from earlier walks.
+ * bh_sorted_forces: the device address of that array, float4 [n]
+ *   (a.x, a.y, a.z, phi) in sorted body order, inside the bound workspace;
+ *   the caller fills in the other ranks' body ranges before bh_step_end.
+ * bh_step_end: the corrector of every body with the sorted force array
+ *   (init as in bh_step_begin).
+ * Out of order calls return BH_ERR_STATE.  Walking every group once and
+ * calling bh_step_end gives exactly bh_step's result. */
+int bh_step_begin(bh_ctx *ctx, double dt, int32_t init, void *stream);
+int bh_walk_groups(bh_ctx *ctx, float theta, float eps, int32_t g_begin, int32_t g_end, void *stream);
+int bh_sorted_forces(bh_ctx *ctx, float **acc_dev);
+int bh_step_end(bh_ctx *ctx, double dt, int32_t init, void *stream);
+
 /* Energies and momentum of the current state (FP64, synchronises):
  * out[0] kinetic, out[1] potential = 1/2 sum m phi, out[2..4] momentum.
  * The potentials are those of the last force evaluation. */

@@ -128,6 +128,11 @@ _SIG = {
                      ctypes.c_void_p],
     "bh_step": [ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_float, ctypes.c_void_p],
     "bh_step_graph": [ctypes.c_void_p, ctypes.c_double, ctypes.c_float, ctypes.c_float, ctypes.c_void_p],
+    "bh_step_begin": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p],
+    "bh_walk_groups": [ctypes.c_void_p, ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_int32,
+                       ctypes.c_void_p],
+    "bh_sorted_forces": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)],
+    "bh_step_end": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_void_p],
     "bh_diagnostics": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "bh_block_start": [ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_float,
                        ctypes.c_float, ctypes.c_void_p],
@@ -378,6 +383,44 @@ class TreeCode:
     def step(self, dt: float, theta: float, eps: float, graph: bool = False, stream=None):
         f = self.lib.bh_step_graph if graph else self.lib.bh_step
         _check(f(self.ctx, float(dt), float(theta), float(eps), _stream(stream)), "bh_step")
+
+    # ---- the step in parts (groups shared out among ranks: see shard.py)
+    def step_begin(self, dt: float, init: bool = False, stream=None):
+        _check(self.lib.bh_step_begin(self.ctx, float(dt), int(init), _stream(stream)), "bh_step_begin")
+
+    def walk_groups(self, theta: float, eps: float, g_begin: int, g_end: int, stream=None):
+        _check(self.lib.bh_walk_groups(self.ctx, float(theta), float(eps), int(g_begin), int(g_end),
+                                       _stream(stream)), "bh_walk_groups")
+
+    def step_end(self, dt: float, init: bool = False, stream=None):
+        _check(self.lib.bh_step_end(self.ctx, float(dt), int(init), _stream(stream)), "bh_step_end")
+
+    def sorted_forces(self):
+        """The context's sorted force array as a float32 [n, 4] CUDA tensor
+        (a view of the workspace: a.x, a.y, a.z, phi per sorted body)."""
+        import torch
+
+        ptr = ctypes.c_void_p()
+        _check(self.lib.bh_sorted_forces(self.ctx, ctypes.byref(ptr)), "bh_sorted_forces")
+        n = self.counts()["n"]
+        off = ptr.value - self.workspace.data_ptr()
+        if off < 0 or off % 16 or off + 16 * n > self.workspace.numel():
+            raise RuntimeError("bh_sorted_forces: address outside the bound workspace")
+        return self.workspace[off:off + 16 * n].view(torch.float32).view(n, 4)
+
+    def group_begins(self, stream=None):
+        """Sorted first body of each group of the last build, then the end: int64 [G + 1]."""
+        import numpy as np
+
+        G = self.counts(stream)["groups"]
+        if G == 0:
+            return np.zeros(1, np.int64)
+        gb = np.zeros(G, np.int32)
+        ge = np.zeros(G, np.int32)
+        nul = [None] * 9
+        _check(self.lib.bh_get_tree(self.ctx, *nul, gb.ctypes.data_as(ctypes.c_void_p),
+                                    ge.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "bh_get_tree")
+        return np.concatenate([gb.astype(np.int64), ge[-1:].astype(np.int64)])
 
     def diagnostics(self, stream=None):
         out = (ctypes.c_double * 5)()

@@ -295,6 +295,7 @@ int check_theta_eps(float theta, float eps) {
 // One leapfrog step (init: evaluate the accelerations at the loaded state only).
 int step_impl(Ctx &c, double dt, float theta, float eps, bool init, cudaStream_t s) {
   cudaError_t e;
+  c.split_open = false;  // a whole step ends any step in parts
   if (c.n == 0) return BH_OK;
   if (!init) {
     Phase ph(c, s, 6);
@@ -622,6 +623,80 @@ int bh_step_graph(bh_ctx *ctx, double dt, float theta, float eps, void *stream) 
   }
   c.launches += c.graph_launches[par];
   return cu(cudaGraphLaunch(c.graph_exec[par], s));
+}
+
+int bh_step_begin(bh_ctx *ctx, double dt, int32_t init, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.have_state) return BH_ERR_STATE;
+  if (!std::isfinite(dt) || (init != 0 && init != 1)) return BH_ERR_INVALID_ARG;
+  if (!init && !c.have_acc) return BH_ERR_STATE;  // the accelerations at the loaded state come first
+  DeviceGuard g(c.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c.block_on = c.block_tree = false;
+  c.split_open = false;
+  if (c.n == 0) {
+    c.split_open = true;
+    c.split_init = init;
+    return BH_OK;
+  }
+  cudaError_t e;
+  if (!init) {
+    Phase ph(c, s, 6);
+    if ((e = bh::launch_predict(c, dt, s))) return cu(e);
+  }
+  const int a = c.state_cur;
+  if ((rc = build_pipeline(c, c.st_x[a], c.st_m[a], kMoveState, s))) return rc;
+  c.built = true;
+  c.split_open = true;
+  c.split_init = init;
+  return BH_OK;
+}
+
+int bh_walk_groups(bh_ctx *ctx, float theta, float eps, int32_t g_begin, int32_t g_end, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.split_open) return BH_ERR_STATE;
+  if ((rc = check_theta_eps(theta, eps))) return rc;
+  if (g_begin < 0 || g_end < g_begin) return BH_ERR_INVALID_ARG;
+  if (c.n == 0 || g_end == g_begin) return BH_OK;
+  DeviceGuard g(c.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = bh::launch_mark_groups(c, g_begin, g_end, s))) return cu(e);
+  if ((rc = walk_phase(c, theta, eps, bh::kOutSorted, nullptr, nullptr, s, c.g_active))) return rc;
+  c.forces = true;  // (the walked groups' statistics are exported by bh_get_group_stats)
+  return BH_OK;
+}
+
+int bh_sorted_forces(bh_ctx *ctx, float **acc_dev) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  if (!acc_dev) return BH_ERR_INVALID_ARG;
+  *acc_dev = reinterpret_cast<float *>(ctx->c.acc_sorted);
+  return BH_OK;
+}
+
+int bh_step_end(bh_ctx *ctx, double dt, int32_t init, void *stream) {
+  int rc = ready(ctx);
+  if (rc) return rc;
+  Ctx &c = ctx->c;
+  if (!c.split_open) return BH_ERR_STATE;
+  if (init != c.split_init || !std::isfinite(dt)) return BH_ERR_INVALID_ARG;
+  DeviceGuard g(c.device);
+  cudaStream_t s = (cudaStream_t)stream;
+  c.split_open = false;
+  if (init) c.have_acc = true;
+  if (c.n == 0) return BH_OK;
+  {
+    Phase ph(c, s, 6);
+    cudaError_t e = bh::launch_correct(c, init ? 0.0 : dt, s);
+    if (e) return cu(e);
+  }
+  c.forces = true;
+  return BH_OK;
 }
 
 int bh_block_start(bh_ctx *ctx, double dt_max, int32_t k_max, double eta, float theta, float eps, void *stream) {

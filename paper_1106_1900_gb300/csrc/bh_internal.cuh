@@ -53,6 +53,8 @@ struct Ctx {
   bool forces = false;      // bh_compute_forces done since build
   bool have_state = false;  // bh_set_state done
   bool have_acc = false;    // a_old valid for the state
+  bool split_open = false;  // bh_step_begin done, bh_step_end not yet
+  int split_init = 0;       // ... for the initial force evaluation
   int state_cur = 0;        // which state buffer (0/1) is current
   // block time-steps: levels k (steps dt_max 2^-k) on integer ticks of dt_max 2^-k_max
   bool block_on = false;    // bh_block_start done since the state was loaded
@@ -167,6 +169,7 @@ enum OutMode { kOutCaller = 0, kOutSorted = 1 };
 cudaError_t launch_walk(Ctx &c, float theta, float eps, OutMode mode, float *acc, float *pot, cudaStream_t s,
                         const uint8_t *g_active = nullptr);
 int walk_smem_bytes(int warps);
+cudaError_t launch_mark_groups(Ctx &c, int g0, int g1, cudaStream_t s);  // g_active = [g0, g1)
 int walk_list_stride(const bh_params &p);  // ints of list scratch per walking warp
 void walk_grids(int *trav_blocks_per_sm, int *eval_blocks_per_sm, int *fused_blocks_per_sm);
 // the fused walk unless the split form is asked for or the FP64 evaluation needs the pool

@@ -1312,6 +1312,22 @@ cudaError_t launch_fused(Ctx &c, const TravArgs &t, const EvalArgs &a, cudaStrea
 
 }  // namespace
 
+namespace {
+// g_active[g] = 1 for groups g0 <= g < g1 of the last build, else 0.
+__global__ void __launch_bounds__(256) k_mark_groups(const int32_t *__restrict__ counts, int g0, int g1,
+                                                     uint8_t *g_active) {
+  const int G = counts[1];
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x)
+    g_active[g] = (g >= g0 && g < g1) ? 1 : 0;
+}
+}  // namespace
+
+cudaError_t launch_mark_groups(Ctx &c, int g0, int g1, cudaStream_t s) {
+  k_mark_groups<<<c.num_sms * 4, 256, 0, s>>>(c.d_counts, g0, g1, c.g_active);
+  c.launches++;
+  return cudaGetLastError();
+}
+
 int walk_smem_bytes(int warps) { return warps * (int)sizeof(EvalSmem); }
 
 // Ints of list scratch per walking warp: the fused walk's buffers, or for

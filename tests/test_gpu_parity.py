@@ -383,6 +383,76 @@ def test_min_distance_mac_forest(cuda_lib):
     _full_parity(cuda_lib, pos, m, 0.6, 0.01, offsets=off, mac=1)
 
 
+def test_step_in_parts_two_ranks_equal_one_step(cuda_lib):
+    """One system's groups shared out among two "ranks" (two contexts on one
+    GPU, run one after the other): each builds the same tree, walks its own
+    group range, the walked bodies' forces are exchanged and both correct
+    every body.  Four steps (the initial evaluation and three leapfrog
+    steps, the split balanced by the previous step's counts) equal the
+    one-context leapfrog bit for bit, on both ranks."""
+    import torch
+
+    from paper_1106_1900_gb300 import shard
+
+    pos, vel, m = ics.plummer(30000, 41)
+    n, theta, eps, dt = len(pos), 0.5, 0.01, 1 / 64
+    kw = dict(n_leaf=8, n_crit=64, list_buffer=1024)
+    ref = cuda_lib.TreeCode(n, **kw)
+    ref.set_state(_dev(pos), _dev(vel), _dev(m))
+    for _ in range(3):
+        ref.step(dt, theta, eps)
+    ranks = []
+    for _ in range(2):
+        tc = cuda_lib.TreeCode(n, **kw)
+        tc.set_state(_dev(pos), _dev(vel), _dev(m))
+        ranks.append(tc)
+    prev = None
+    for k in range(4):
+        init, h = k == 0, (0.0 if k == 0 else dt)
+        for tc in ranks:
+            tc.step_begin(h, init=init)
+        gbeg = ranks[0].group_begins()
+        assert np.array_equal(gbeg, ranks[1].group_begins())
+        ranges = shard.split_groups(shard.group_costs(gbeg, prev), 2)
+        assert ranges[0][1] > 0 and ranges[1][0] < len(gbeg) - 1  # both ranks walk
+        for r, tc in enumerate(ranks):
+            tc.walk_groups(theta, eps, *ranges[r])
+        f = [tc.sorted_forces() for tc in ranks]
+        (a0, a1), (b0, b1) = ((int(gbeg[g0]), int(gbeg[g1])) for g0, g1 in ranges)
+        f[0][b0:b1] = f[1][b0:b1]
+        f[1][a0:a1] = f[0][a0:a1]
+        st = [tc.group_stats() for tc in ranks]
+        npp = np.concatenate([st[0]["np"][:ranges[0][1]], st[1]["np"][ranges[1][0]:]])
+        npc = np.concatenate([st[0]["nc"][:ranges[0][1]], st[1]["nc"][ranges[1][0]:]])
+        prev = shard.body_costs(gbeg, npc, npp)
+        for tc in ranks:
+            tc.step_end(h, init=init)
+    want = [torch.empty((n, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+    ref.get_state(*want)
+    for tc in ranks:
+        tc.check()
+        got = [torch.empty((n, 3), dtype=torch.float64, device="cuda") for _ in range(2)]
+        tc.get_state(*got)
+        assert torch.equal(got[0], want[0]) and torch.equal(got[1], want[1])
+
+
+def test_step_in_parts_order_is_checked(cuda_lib):
+    pos, vel, m = ics.plummer(2000, 42)
+    tc = cuda_lib.TreeCode(2000)
+    tc.set_state(_dev(pos), _dev(vel), _dev(m))
+    with pytest.raises(cuda_lib.BHError) as e:
+        tc.walk_groups(0.5, 0.01, 0, 10)  # no step begun
+    assert e.value.code == 6
+    with pytest.raises(cuda_lib.BHError):
+        tc.step_begin(1 / 64, init=False)  # the initial evaluation first
+    tc.step_begin(0.0, init=True)
+    with pytest.raises(cuda_lib.BHError):
+        tc.step_end(0.0, init=False)  # begun as the initial evaluation
+    tc.walk_groups(0.5, 0.01, 0, 1 << 30)  # every group (the end is clamped)
+    tc.step_end(0.0, init=True)
+    tc.check()
+
+
 def test_forest_step_equals_systems(cuda_lib):
     pos, vel, m, off = ics.ensemble(n_sys=6, seed=7, n_min=500, n_max=4000)
     _, xf, vf, _, _ = _state_run(cuda_lib, pos, vel, m, 3, 1 / 64, 0.5, 0.01, offsets=off)
@@ -466,8 +536,26 @@ def test_autotune_keeps_error_and_picks_fastest(cuda_lib):
 
     pos, vel, m = ics.plummer(30000, 3)
     P_, V_, M_ = (torch.from_numpy(a).cuda() for a in (pos, vel, m))
-    best, trials = autotune.autotune(P_, V_, M_, 0.5, 0.01, grid=[(8, 16), (16, 32)], steps=2, subsample=1024)
+    best, trials = autotune.autotune(P_, V_, M_, 0.5, 0.01, grid=[(8, 16), (16, 32)], steps=2, subsample=1024,
+                                     walk_grid=[(1024, 6), (4096, 5)])
     paper = next(r for r in trials if (r["n_leaf"], r["n_crit"]) == autotune.PAPER_PAIR)
     assert best["p99"] <= paper["p99"] * 1.05
     assert best["ms_per_step"] == min(r["ms_per_step"] for r in trials if r["p99"] <= paper["p99"] * 1.05)
     assert 1e-6 < paper["p50"] < 1e-3  # a quadrupole tree at theta = 0.5
+    # the walk stage keeps the chosen pair and tries the buffer and warp settings
+    walk = [r for r in trials if r.get("stage") == "walk"]
+    assert len(walk) == 2 and all("list_buffer" in r for r in walk)
+
+
+def test_autotune_forest_reference_is_per_system(cuda_lib):
+    """The forest's error reference sums each target's own system only."""
+    import torch
+
+    from paper_1106_1900_gb300 import autotune
+
+    pos, vel, m, off = ics.ensemble(n_sys=8, seed=12, n_min=500, n_max=3000)
+    P_, M_ = torch.from_numpy(pos).cuda(), torch.from_numpy(m).cuda()
+    tg = np.sort(np.random.default_rng(1).choice(len(pos), 300, replace=False)).astype(np.int32)
+    ref = autotune.reference(P_, M_, 0.01, torch.from_numpy(tg).cuda(), off).cpu().numpy()
+    ad, _ = oracle.direct(pos, m, 0.01, targets=tg, offsets=off)
+    assert np.max(np.linalg.norm(ref - ad, axis=1) / np.linalg.norm(ad, axis=1)) < 1e-4

@@ -69,11 +69,15 @@ def test_precision_study_1m(cuda_lib):
 
 
 def test_energy_drift_100_steps(cuda_lib):
+    """Leapfrog energy drift (Eq. 3) of the 1M Plummer sphere over 100 steps
+    of dt = 1/64, theta = 0.5, in the benchmark's configuration."""
     import torch
 
-    n = 1 << 18
+    from paper_1106_1900_gb300 import autotune
+
+    n = 1 << 20
     pos, vel, m = ics.plummer(n, 4)
-    tc = cuda_lib.TreeCode(n)
+    tc = cuda_lib.TreeCode(n, **(autotune.tuned_params(n, 0.5, "plummer") or {}))
     tc.set_state(*(torch.from_numpy(a).cuda() for a in (pos, vel, m)))
     tc.step(0.0, 0.5, 0.005, graph=False)  # forces at t = 0
     d0 = tc.diagnostics()
@@ -85,7 +89,7 @@ def test_energy_drift_100_steps(cuda_lib):
         d = tc.diagnostics()
         worst = max(worst, abs((e0 - (d["ekin"] + d["epot"])) / e0))
     tc.check()
-    print(f"\nenergy: E0 = {e0:.6f}, max |dE/E0| over 100 steps = {worst:.3e}, momentum = {d['mom']}")
+    print(f"\nenergy (N = {n}): E0 = {e0:.6f}, max |dE/E0| over 100 steps = {worst:.3e}, momentum = {d['mom']}")
     assert -0.27 < e0 < -0.23  # Plummer in virial units: E = -1/4
     assert worst < 1e-3
     assert max(abs(x) for x in d["mom"]) < 1e-4
