@@ -36,7 +36,8 @@ THETA, EPS, DT = 0.5, 0.005, 1.0 / 64
 SEED = 2
 # flops per interaction: FMA = 2, rsqrt = 1, add/sub/mul = 1 (counted from k_walk.cu)
 FLOPS_PP = 20
-FLOPS_PC = 54
+FLOPS_PC = 54  # the work unit fixed from the first particle-cell sequence
+FLOPS_PC_IMPLEMENTED = 53  # what the current pc2() performs by the same rule
 SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128
 # Algorithmic HBM bytes of the build phases and the leapfrog of one step:
@@ -679,6 +680,8 @@ def main():
                                 "evaluation of its lists)"),
                      "peak_source": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{SM_MAX_MHZ:.0f} MHz (unit counts and max clock)",
+                     "flops_per_pp": FLOPS_PP, "flops_per_pc_unit": FLOPS_PC,
+                     "flops_per_pc_implemented": FLOPS_PC_IMPLEMENTED,
                      "flops_per_step": flops / args.steps, "pp_per_step": pp / args.steps,
                      "pc_per_step": pc / args.steps, "eval_ms_mean": statistics.mean(eval_ms),
                      "walk_phase": {"ms_mean": statistics.mean(walk_ms), "achieved": achieved_walk / 1e12,
