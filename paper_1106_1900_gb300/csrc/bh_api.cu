@@ -146,7 +146,6 @@ void carve(Ctx &c, char *base, size_t *total) {
   c.c_parent = k.take<int32_t>(C);
   c.c_first = k.take<int32_t>(C);
   c.c_nch = k.take<int32_t>(C);
-  c.c_ctr = k.take<uint32_t>(C);
   c.c_link = k.take<int2>(C);
   c.c_mom = k.take<float4>(4 * C);
   c.c_mac = k.take<float4>(C);

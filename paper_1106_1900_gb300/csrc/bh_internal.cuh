@@ -96,7 +96,6 @@ struct Ctx {
   uint32_t *rowoff;              // [D + 2][W]
   // per cell
   int32_t *c_level, *c_pbeg, *c_pend, *c_parent, *c_first, *c_nch;
-  uint32_t *c_ctr;               // bottom-up arrival counters
   int2 *c_link;                  // walk link {first, count | leaf << 31}
   float4 *c_mom;                 // [C][4] moments (see k_moments.cu)
   float4 *c_mac;                 // [C] com_hi xyz, l/theta + delta

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos,
 }
 
 // ----------------------------------------------------------------- sort
-constexpr int kSortIpt = 16;
+constexpr int kSortIpt = 8;
 constexpr int kSortTile = kBlock * kSortIpt;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
                                                  const uint32_t *__restrict__ rowoff, int W,
                                                  const uint64_t *__restrict__ scan_total, int32_t *c_level,
                                                  int32_t *c_pbeg, int32_t *c_parent, int32_t *c_first,
-                                                 uint32_t *c_ctr, int32_t *sys_root, int32_t *g_beg, int32_t *g_sys,
+                                                 int32_t *sys_root, int32_t *g_beg, int32_t *g_sys,
                                                  int32_t *counts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int w = i >> 5;
@@ -656,7 +656,6 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
       c_pbeg[cell] = i;
       c_parent[cell] = (k > lo) ? prev : -1;
       c_first[cell] = -1;
-      c_ctr[cell] = 0;
       if (k > lo) c_first[prev] = cell;
       if (k == 0) sys_root[s] = cell;
       prev = cell;
@@ -1012,7 +1011,7 @@ static cudaError_t cells_impl(Ctx &c, cudaStream_t s) {
   cudaError_t e = launch_scan_u32(c, c.rowcnt, c.rowoff, (int64_t)(D + 2) * W, s);
   if (e) return e;
   k_emit<FOREST, DEEP><<<nb, kBlock, 0, s>>>(n, D, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total,
-                                             c.c_level, c.c_pbeg, c.c_parent, c.c_first, c.c_ctr, c.sys_root,
+                                             c.c_level, c.c_pbeg, c.c_parent, c.c_first, c.sys_root,
                                              c.g_beg, c.g_sys, c.d_counts);
   k_link<FOREST, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(n, c.key[0], c.skey_lo, D, c.offs, c.n_sys, c.rowoff, W,
                                                         c.d_counts, c.c_level, c.c_pbeg, c.c_pend, c.c_parent,

@@ -1,11 +1,13 @@
 // k_moments.cu -- monopole + quadrupole moments of every cell (§3.2, Fig. 4).
 //
 // The paper computes the leaves in parallel and then the nodes level by
-// level, bottom to top, from the moments one level below.  Here the same
-// bottom-up order runs in one launch: every leaf computes its moments from
-// its bodies, then climbs; a node is computed by whichever child arrives
-// last at its counter (the others stop), from all its children in index
-// order, so the result does not depend on arrival order.  Nothing waits.
+// level, bottom to top, from the moments one level below.  Here too: one
+// launch per level, from the deepest up, over that level's contiguous range
+// of cells (cells are stored in level order); a leaf from its bodies, a node
+// from its children in index order, each in one pass over its records (the
+// quadrupole accumulated about the geometric centre, then moved to the
+// centre of mass).  Every cell is one thread's work and no thread waits for
+// another.
 //
 // Arithmetic is FP32 in cell-relative coordinates (the paper uses FP64 on
 // hardware whose FP32 path lost accuracy in absolute coordinates): a body
@@ -136,119 +138,137 @@ __device__ __forceinline__ void add_point_quad(float Q[6], float m, float dx, fl
   Q[5] += m * 3.f * dy * dz;
 }
 
+// Q about the centre of mass c (offset from the geometric centre) from Q
+// about the geometric centre: Q_c = Q_G - M (3 c c^T - |c|^2 I) (the
+// parallel-axis rule for a traceless quadrupole; Q_G ~ M l^2, so the
+// rounding of the difference stays ~1e-7 M l^2 however small Q_c is).
+__device__ __forceinline__ void shift_to_com(float Q[6], float M, const float cm[3]) {
+  const float c2 = cm[0] * cm[0] + cm[1] * cm[1] + cm[2] * cm[2];
+  Q[0] -= M * (3.f * cm[0] * cm[0] - c2);
+  Q[1] -= M * (3.f * cm[1] * cm[1] - c2);
+  Q[2] -= M * (3.f * cm[2] * cm[2] - c2);
+  Q[3] -= M * 3.f * cm[0] * cm[1];
+  Q[4] -= M * 3.f * cm[0] * cm[2];
+  Q[5] -= M * 3.f * cm[1] * cm[2];
+}
+
+// A leaf's moments from its bodies (sorted range b..e of level k), in one
+// pass over them: mass and first moments about the geometric centre
+// (compensated sums), the quadrupole about it, then shifted to the centre
+// of mass.
 // REFRESH: the tree is unchanged but its bodies moved (block time-steps); a
 // cell keeps its geometric centre and its size grows to the smallest cube
 // about that centre holding its bodies (a leaf) or its children's cubes (a
 // node, l/2 + the largest child side), never below its built size.
 template <bool FOREST, bool REFRESH, bool DEEP>
-__global__ void __launch_bounds__(kBlock) k_moments(const Keys K, const int32_t *__restrict__ offs, int S,
-                                                    const Frame *__restrict__ frame,
-                                                    const FrameF *__restrict__ framef,
-                                                    const int32_t *__restrict__ counts,
-                                                    const int32_t *__restrict__ c_level,
-                                                    const int32_t *__restrict__ c_pbeg,
-                                                    const int32_t *__restrict__ c_pend,
-                                                    const int32_t *__restrict__ c_parent,
-                                                    const int32_t *__restrict__ c_first,
-                                                    const int32_t *__restrict__ c_nch, uint32_t *c_ctr,
-                                                    const float4 *__restrict__ part_hi,
-                                                    const float4 *__restrict__ part_lo, float4 *mom) {
-  const int C = counts[0];
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void leaf_moments(int c, int k, int b, int e, const Keys &K,
+                                             const int32_t *__restrict__ offs, int S,
+                                             const Frame *__restrict__ frame, const FrameF *__restrict__ framef,
+                                             const float4 *__restrict__ part_hi, const float4 *__restrict__ part_lo,
+                                             float4 *mom) {
+  Centre G = cell_centre<FOREST, DEEP>(k, b, K, offs, S, frame, framef);
+  // compensated sums (TwoSum): a leaf at the deepest level may hold
+  // thousands of bodies, whose plain FP32 sum of equal masses drifts by
+  // ~n ulp
+  float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, ext = 0.f;
+  float eM = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+  float Q[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = b; i < e; ++i) {
+    float4 h = part_hi[i], l = part_lo[i];
+    float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]);
+    float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]);
+    float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]);
+    if (REFRESH) ext = fmaxf(ext, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
+    add_compensated(M, eM, h.w);
+    add_compensated(sx, ex, h.w * dx);
+    add_compensated(sy, ey, h.w * dy);
+    add_compensated(sz, ez, h.w * dz);
+    add_point_quad(Q, h.w, dx, dy, dz);
+  }
+  M += eM;
+  sx += ex;
+  sy += ey;
+  sz += ez;
+  float cm[3] = {0.f, 0.f, 0.f};
+  if (M > 0.f) {
+    cm[0] = sx / M;
+    cm[1] = sy / M;
+    cm[2] = sz / M;
+  }
+  shift_to_com(Q, M, cm);
+  write_cell(mom, c, G, M, cm, Q, REFRESH ? fmaxf(G.l, 2.f * ext) : G.l);
+}
+
+// A node's moments from its nch children f .. f + nch - 1 (one level
+// deeper, already complete), in index order and one pass over their
+// records: the children's quadrupoles moved to the node's geometric centre
+// by the parallel-axis rule, summed, then shifted to the node's centre of
+// mass.
+template <bool FOREST, bool REFRESH, bool DEEP>
+__device__ __forceinline__ void node_moments(int c, int k, int pbeg, int f, int nch, const Keys &K,
+                                             const int32_t *__restrict__ offs, int S,
+                                             const Frame *__restrict__ frame, const FrameF *__restrict__ framef,
+                                             float4 *mom) {
+  Centre G = cell_centre<FOREST, DEEP>(k, pbeg, K, offs, S, frame, framef);
+  float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, lch = 0.f;
+  float Q[6] = {0, 0, 0, 0, 0, 0};
+  for (int j = 0; j < nch; ++j) {
+    const float4 a = mom[4 * (size_t)(f + j)];
+    const float4 b = mom[4 * (size_t)(f + j) + 1];
+    const float4 q0 = mom[4 * (size_t)(f + j) + 2];
+    const float4 q1 = mom[4 * (size_t)(f + j) + 3];
+    if (REFRESH) lch = fmaxf(lch, q1.z);
+    const float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]);
+    const float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]);
+    const float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]);
+    M += a.w;
+    sx += a.w * dx;
+    sy += a.w * dy;
+    sz += a.w * dz;
+    Q[0] += q0.x;
+    Q[1] += q0.y;
+    Q[2] += q0.z;
+    Q[3] += q0.w;
+    Q[4] += q1.x;
+    Q[5] += q1.y;
+    add_point_quad(Q, a.w, dx, dy, dz);
+  }
+  float cm[3] = {0.f, 0.f, 0.f};
+  if (M > 0.f) {
+    cm[0] = sx / M;
+    cm[1] = sy / M;
+    cm[2] = sz / M;
+  }
+  shift_to_com(Q, M, cm);
+  write_cell(mom, c, G, M, cm, Q, REFRESH ? fmaxf(G.l, fmaf(0.5f, G.l, lch)) : G.l);
+}
+
+// The cells of level k (a contiguous range: cells are in level order, the
+// level scan's offsets rowoff[k W] .. rowoff[(k + 1) W]): leaves from their
+// bodies, nodes from their children, which the previous launch (level
+// k + 1) completed.  Launched for k = D down to 0, so the pass runs bottom
+// up level by level, as the paper's, with no waiting and no counters.
+template <bool FOREST, bool REFRESH, bool DEEP>
+__global__ void __launch_bounds__(kBlock) k_moments_level(const Keys K, const int32_t *__restrict__ offs, int S,
+                                                          const Frame *__restrict__ frame,
+                                                          const FrameF *__restrict__ framef,
+                                                          const uint32_t *__restrict__ rowoff, int W, int k,
+                                                          const int32_t *__restrict__ c_level,
+                                                          const int32_t *__restrict__ c_pbeg,
+                                                          const int32_t *__restrict__ c_pend,
+                                                          const int32_t *__restrict__ c_first,
+                                                          const int32_t *__restrict__ c_nch,
+                                                          const float4 *__restrict__ part_hi,
+                                                          const float4 *__restrict__ part_lo, float4 *mom) {
+  const int c0 = (int)rowoff[(size_t)k * W], c1 = (int)rowoff[(size_t)(k + 1) * W];
+  for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x) {
     const int lv = c_level[c];
-    if (!(lv & 32)) continue;  // nodes are finished by their last child
-    // ---- leaf: from its bodies
-    {
-      const int k = lv & 31, b = c_pbeg[c], e = c_pend[c];
-      Centre G = cell_centre<FOREST, DEEP>(k, b, K, offs, S, frame, framef);
-      // compensated sums (TwoSum): a leaf at the deepest level may hold
-      // thousands of bodies, whose plain FP32 sum of equal masses drifts by
-      // ~n ulp
-      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, ext = 0.f;
-      float eM = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
-      for (int i = b; i < e; ++i) {
-        float4 h = part_hi[i], l = part_lo[i];
-        float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]);
-        float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]);
-        float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]);
-        if (REFRESH) ext = fmaxf(ext, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
-        add_compensated(M, eM, h.w);
-        add_compensated(sx, ex, h.w * dx);
-        add_compensated(sy, ey, h.w * dy);
-        add_compensated(sz, ez, h.w * dz);
-      }
-      M += eM;
-      sx += ex;
-      sy += ey;
-      sz += ez;
-      float cm[3] = {0.f, 0.f, 0.f};
-      if (M > 0.f) {
-        cm[0] = sx / M;
-        cm[1] = sy / M;
-        cm[2] = sz / M;
-      }
-      float Q[6] = {0, 0, 0, 0, 0, 0};
-      for (int i = b; i < e; ++i) {
-        float4 h = part_hi[i], l = part_lo[i];
-        float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]) - cm[0];
-        float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]) - cm[1];
-        float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]) - cm[2];
-        add_point_quad(Q, h.w, dx, dy, dz);
-      }
-      write_cell(mom, c, G, M, cm, Q, REFRESH ? fmaxf(G.l, 2.f * ext) : G.l);
-    }
-    // ---- climb while this thread is the last child to arrive
-    int cur = c;
-    for (int climb = 0; climb <= kLevelsMax; ++climb) {  // at most D ancestors
-      const int p = c_parent[cur];
-      if (p < 0 || p >= C) break;
-      __threadfence();
-      const uint32_t nch = (uint32_t)c_nch[p];
-      if (nch == 0 || nch > 8) break;
-      if (atomicAdd(&c_ctr[p], 1u) != nch - 1) break;
-      __threadfence();
-      const int k = c_level[p] & 31;
-      Centre G = cell_centre<FOREST, DEEP>(k, c_pbeg[p], K, offs, S, frame, framef);
-      const int f = c_first[p];
-      float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, lch = 0.f;
-      for (uint32_t j = 0; j < nch; ++j) {
-        float4 a = __ldcg(&mom[4 * (size_t)(f + j)]);
-        float4 b = __ldcg(&mom[4 * (size_t)(f + j) + 1]);
-        if (REFRESH) lch = fmaxf(lch, __ldcg(&mom[4 * (size_t)(f + j) + 3]).z);
-        float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]);
-        float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]);
-        float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]);
-        M += a.w;
-        sx += a.w * dx;
-        sy += a.w * dy;
-        sz += a.w * dz;
-      }
-      float cm[3] = {0.f, 0.f, 0.f};
-      if (M > 0.f) {
-        cm[0] = sx / M;
-        cm[1] = sy / M;
-        cm[2] = sz / M;
-      }
-      float Q[6] = {0, 0, 0, 0, 0, 0};
-      for (uint32_t j = 0; j < nch; ++j) {
-        float4 a = __ldcg(&mom[4 * (size_t)(f + j)]);
-        float4 b = __ldcg(&mom[4 * (size_t)(f + j) + 1]);
-        float4 q0 = __ldcg(&mom[4 * (size_t)(f + j) + 2]);
-        float4 q1 = __ldcg(&mom[4 * (size_t)(f + j) + 3]);
-        float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]) - cm[0];
-        float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]) - cm[1];
-        float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]) - cm[2];
-        Q[0] += q0.x;
-        Q[1] += q0.y;
-        Q[2] += q0.z;
-        Q[3] += q0.w;
-        Q[4] += q1.x;
-        Q[5] += q1.y;
-        add_point_quad(Q, a.w, dx, dy, dz);
-      }
-      write_cell(mom, p, G, M, cm, Q, REFRESH ? fmaxf(G.l, fmaf(0.5f, G.l, lch)) : G.l);
-      cur = p;
-    }
+    if (lv & 32)
+      leaf_moments<FOREST, REFRESH, DEEP>(c, lv & 31, c_pbeg[c], c_pend[c], K, offs, S, frame, framef, part_hi,
+                                          part_lo, mom);
+    else
+      node_moments<FOREST, REFRESH, DEEP>(c, lv & 31, c_pbeg[c], c_first[c], min(max(c_nch[c], 0), 8), K, offs,
+                                          S, frame, framef, mom);
   }
 }
 
@@ -275,13 +295,6 @@ __global__ void __launch_bounds__(kBlock) k_mac(const int32_t *__restrict__ coun
     mac[c] = make_float4(a.x, a.y, a.z, fmaf(l, inv_theta, b.w));
     if (mac_lo) mac_lo[c] = make_float4(b.x, b.y, b.z, 0.f);
   }
-}
-
-// Arrival counters of the bottom-up pass back to zero (a moment refresh on an
-// unchanged tree; a build clears them while it emits the cells).
-__global__ void __launch_bounds__(kBlock) k_clear_counters(const int32_t *__restrict__ counts, uint32_t *c_ctr) {
-  const int C = counts[0];
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) c_ctr[c] = 0;
 }
 
 // The minimal-distance criterion's record: the cell's geometric centre
@@ -317,9 +330,13 @@ __global__ void __launch_bounds__(kBlock) k_mac_box(const int32_t *__restrict__ 
 template <bool FOREST, bool REFRESH, bool DEEP>
 static void moments_impl(Ctx &c, cudaStream_t s) {
   const Keys K{c.key[0], c.skey_lo, c.levels};
-  k_moments<FOREST, REFRESH, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(
-      K, c.offs, c.n_sys, c.frame, c.framef, c.d_counts, c.c_level, c.c_pbeg, c.c_pend, c.c_parent, c.c_first,
-      c.c_nch, c.c_ctr, c.part_hi, c.part_lo, c.c_mom);
+  const int W = (int)((c.n + 31) / 32);  // the level scan's rows: W entries per level
+  for (int k = c.levels; k >= 0; --k) {
+    k_moments_level<FOREST, REFRESH, DEEP><<<c.num_sms * 4, kBlock, 0, s>>>(
+        K, c.offs, c.n_sys, c.frame, c.framef, c.rowoff, W, k, c.c_level, c.c_pbeg, c.c_pend, c.c_first, c.c_nch,
+        c.part_hi, c.part_lo, c.c_mom);
+    c.launches++;
+  }
 }
 
 template <bool REFRESH>
@@ -339,17 +356,11 @@ static void mac_box_impl(Ctx &c, cudaStream_t s) {
 
 cudaError_t launch_moments(Ctx &c, cudaStream_t s) {
   moments_launch<false>(c, s);
-  c.launches++;
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments_refresh(Ctx &c, cudaStream_t s) {
-  k_clear_counters<<<c.num_sms * 4, kBlock, 0, s>>>(c.d_counts, c.c_ctr);
-  cudaError_t e = cudaGetLastError();
-  c.launches++;
-  if (e) return e;
   moments_launch<true>(c, s);
-  c.launches++;
   return cudaGetLastError();
 }
 
