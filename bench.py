@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--workload", default="plummer", choices=["plummer", "galaxy", "nested"],
                     help="plummer: N-body Plummer sphere (--n); galaxy: Hernquist sphere + exponential disk, "
                          "8,388,608 bodies")
+    ap.add_argument("--galaxy-n", type=int, default=8388608,
+                    help="galaxy bodies, half sphere and half disk (smaller cases for profiling)")
     return ap.parse_args()
 
 
@@ -524,7 +526,7 @@ def main():
     bh.load()
     eps, dt = EPS, DT
     if args.workload == "galaxy":
-        pos, vel, m = ics.galaxy(4194304, 4194304, 3 + rank)
+        pos, vel, m = ics.galaxy(args.galaxy_n // 2, args.galaxy_n - args.galaxy_n // 2, 3 + rank)
         eps = 0.01
         workload = (f"galaxy: Hernquist sphere (a=1, M=1) + exponential disk (R_d=1, z0=0.1, M=0.2), "
                     f"N={len(pos)} per GPU (seed 3+rank), theta={args.theta}, eps={eps}, dt=1/64")

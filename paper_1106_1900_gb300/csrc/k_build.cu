@@ -320,7 +320,7 @@ __device__ __forceinline__ uint32_t block256_exclusive(uint32_t v, uint32_t *s_w
 // One stable digit pass.  Tiles are taken in launch order from a counter, so
 // every tile's predecessors are already running; each tile publishes its
 // digit counts, then sums its predecessors' (bounded wait), then scatters.
-__global__ void __launch_bounds__(kBlock) k_sort_pass(const uint64_t *__restrict__ kin,
+__global__ void __launch_bounds__(kBlock, 4) k_sort_pass(const uint64_t *__restrict__ kin,
                                                       const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
                                                       uint32_t *__restrict__ vout, int n, int byte,
                                                       const uint32_t *__restrict__ binbase, uint32_t *status,
@@ -896,8 +896,11 @@ static int sort_lo_passes(int D) { return D > kLevels ? (3 * (D - kLevels) + 7) 
 int sort_passes_for(int S, int D) { return sort_lo_passes(D) + 8 + sort_sys_passes(S); }
 
 cudaError_t build_init_attrs() {
-  return cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)((size_t)kSortTile * (8 + 4 + 1)));
+  cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)((size_t)kSortTile * (8 + 4 + 1)));
+  if (e) return e;
+  // four tiles per SM: the largest shared-memory carveout
+  return cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
 

@@ -28,6 +28,7 @@ namespace bh {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kBatch = 4;  // a cell's items (bodies or children) loaded together
 
 struct Centre {
   float hi[3], lo[3];  // geometric centre as a two-float sum (hi + lo to ~2^-48)
@@ -152,38 +153,74 @@ __device__ __forceinline__ void shift_to_com(float Q[6], float M, const float cm
   Q[5] -= M * 3.f * cm[1] * cm[2];
 }
 
-// A leaf's moments from its bodies (sorted range b..e of level k), in one
-// pass over them: mass and first moments about the geometric centre
-// (compensated sums), the quadrupole about it, then shifted to the centre
-// of mass.
+// One cell's moments in one pass over its items: a leaf's bodies (sorted
+// range pbeg .. pend) or a node's nch children first .. first + nch - 1 (one
+// level deeper, already complete), in index order.  A body is an item of
+// mass m at its position with no quadrupole of its own; a child is one of
+// mass M at its centre of mass carrying its quadrupole.  Mass and first
+// moments are taken about the cell's geometric centre in compensated sums
+// (TwoSum: a leaf at the deepest level may hold thousands of bodies, whose
+// plain FP32 sum of equal masses drifts by ~n ulp); the quadrupole is summed
+// about the geometric centre (the items' own plus the parallel-axis term of
+// each item's offset) and moved to the centre of mass at the end.  Items
+// are loaded kBatch at a time, the batch's loads issued together.
 // REFRESH: the tree is unchanged but its bodies moved (block time-steps); a
 // cell keeps its geometric centre and its size grows to the smallest cube
 // about that centre holding its bodies (a leaf) or its children's cubes (a
 // node, l/2 + the largest child side), never below its built size.
 template <bool FOREST, bool REFRESH, bool DEEP>
-__device__ __forceinline__ void leaf_moments(int c, int k, int b, int e, const Keys &K,
-                                             const int32_t *__restrict__ offs, int S,
+__device__ __forceinline__ void cell_moments(int c, int k, bool leaf, int pbeg, int pend, int first, int nch,
+                                             const Keys &K, const int32_t *__restrict__ offs, int S,
                                              const Frame *__restrict__ frame, const FrameF *__restrict__ framef,
                                              const float4 *__restrict__ part_hi, const float4 *__restrict__ part_lo,
                                              float4 *mom) {
-  Centre G = cell_centre<FOREST, DEEP>(k, b, K, offs, S, frame, framef);
-  // compensated sums (TwoSum): a leaf at the deepest level may hold
-  // thousands of bodies, whose plain FP32 sum of equal masses drifts by
-  // ~n ulp
-  float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, ext = 0.f;
+  const Centre G = cell_centre<FOREST, DEEP>(k, pbeg, K, offs, S, frame, framef);
+  const int cnt = leaf ? pend - pbeg : nch;
+  float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
   float eM = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+  float ext = 0.f, lch = 0.f;
   float Q[6] = {0, 0, 0, 0, 0, 0};
-  for (int i = b; i < e; ++i) {
-    float4 h = part_hi[i], l = part_lo[i];
-    float dx = (h.x - G.hi[0]) + (l.x - G.lo[0]);
-    float dy = (h.y - G.hi[1]) + (l.y - G.lo[1]);
-    float dz = (h.z - G.hi[2]) + (l.z - G.lo[2]);
-    if (REFRESH) ext = fmaxf(ext, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
-    add_compensated(M, eM, h.w);
-    add_compensated(sx, ex, h.w * dx);
-    add_compensated(sy, ey, h.w * dy);
-    add_compensated(sz, ez, h.w * dz);
-    add_point_quad(Q, h.w, dx, dy, dz);
+  for (int i0 = 0; i0 < cnt; i0 += kBatch) {
+    float4 A[kBatch], B[kBatch], Q0[kBatch], Q1[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      Q0[j] = Q1[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i0 + j < cnt) {
+        if (leaf) {
+          A[j] = part_hi[pbeg + i0 + j];
+          B[j] = part_lo[pbeg + i0 + j];
+        } else {
+          const size_t r = 4 * (size_t)(first + i0 + j);
+          A[j] = mom[r];
+          B[j] = mom[r + 1];
+          Q0[j] = mom[r + 2];
+          Q1[j] = mom[r + 3];
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if (i0 + j >= cnt) break;
+      const float m = A[j].w;
+      const float dx = (A[j].x - G.hi[0]) + (B[j].x - G.lo[0]);
+      const float dy = (A[j].y - G.hi[1]) + (B[j].y - G.lo[1]);
+      const float dz = (A[j].z - G.hi[2]) + (B[j].z - G.lo[2]);
+      if (REFRESH) {
+        ext = fmaxf(ext, fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))));
+        lch = fmaxf(lch, Q1[j].z);
+      }
+      add_compensated(M, eM, m);
+      add_compensated(sx, ex, m * dx);
+      add_compensated(sy, ey, m * dy);
+      add_compensated(sz, ez, m * dz);
+      Q[0] += Q0[j].x;
+      Q[1] += Q0[j].y;
+      Q[2] += Q0[j].z;
+      Q[3] += Q0[j].w;
+      Q[4] += Q1[j].x;
+      Q[5] += Q1[j].y;
+      add_point_quad(Q, m, dx, dy, dz);
+    }
   }
   M += eM;
   sx += ex;
@@ -196,51 +233,9 @@ __device__ __forceinline__ void leaf_moments(int c, int k, int b, int e, const K
     cm[2] = sz / M;
   }
   shift_to_com(Q, M, cm);
-  write_cell(mom, c, G, M, cm, Q, REFRESH ? fmaxf(G.l, 2.f * ext) : G.l);
-}
-
-// A node's moments from its nch children f .. f + nch - 1 (one level
-// deeper, already complete), in index order and one pass over their
-// records: the children's quadrupoles moved to the node's geometric centre
-// by the parallel-axis rule, summed, then shifted to the node's centre of
-// mass.
-template <bool FOREST, bool REFRESH, bool DEEP>
-__device__ __forceinline__ void node_moments(int c, int k, int pbeg, int f, int nch, const Keys &K,
-                                             const int32_t *__restrict__ offs, int S,
-                                             const Frame *__restrict__ frame, const FrameF *__restrict__ framef,
-                                             float4 *mom) {
-  Centre G = cell_centre<FOREST, DEEP>(k, pbeg, K, offs, S, frame, framef);
-  float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, lch = 0.f;
-  float Q[6] = {0, 0, 0, 0, 0, 0};
-  for (int j = 0; j < nch; ++j) {
-    const float4 a = mom[4 * (size_t)(f + j)];
-    const float4 b = mom[4 * (size_t)(f + j) + 1];
-    const float4 q0 = mom[4 * (size_t)(f + j) + 2];
-    const float4 q1 = mom[4 * (size_t)(f + j) + 3];
-    if (REFRESH) lch = fmaxf(lch, q1.z);
-    const float dx = (a.x - G.hi[0]) + (b.x - G.lo[0]);
-    const float dy = (a.y - G.hi[1]) + (b.y - G.lo[1]);
-    const float dz = (a.z - G.hi[2]) + (b.z - G.lo[2]);
-    M += a.w;
-    sx += a.w * dx;
-    sy += a.w * dy;
-    sz += a.w * dz;
-    Q[0] += q0.x;
-    Q[1] += q0.y;
-    Q[2] += q0.z;
-    Q[3] += q0.w;
-    Q[4] += q1.x;
-    Q[5] += q1.y;
-    add_point_quad(Q, a.w, dx, dy, dz);
-  }
-  float cm[3] = {0.f, 0.f, 0.f};
-  if (M > 0.f) {
-    cm[0] = sx / M;
-    cm[1] = sy / M;
-    cm[2] = sz / M;
-  }
-  shift_to_com(Q, M, cm);
-  write_cell(mom, c, G, M, cm, Q, REFRESH ? fmaxf(G.l, fmaf(0.5f, G.l, lch)) : G.l);
+  float l = G.l;
+  if (REFRESH) l = leaf ? fmaxf(G.l, 2.f * ext) : fmaxf(G.l, fmaf(0.5f, G.l, lch));
+  write_cell(mom, c, G, M, cm, Q, l);
 }
 
 // The cells of level k (a contiguous range: cells are in level order, the
@@ -262,13 +257,10 @@ __global__ void __launch_bounds__(kBlock) k_moments_level(const Keys K, const in
                                                           const float4 *__restrict__ part_lo, float4 *mom) {
   const int c0 = (int)rowoff[(size_t)k * W], c1 = (int)rowoff[(size_t)(k + 1) * W];
   for (int c = c0 + blockIdx.x * blockDim.x + threadIdx.x; c < c1; c += gridDim.x * blockDim.x) {
-    const int lv = c_level[c];
-    if (lv & 32)
-      leaf_moments<FOREST, REFRESH, DEEP>(c, lv & 31, c_pbeg[c], c_pend[c], K, offs, S, frame, framef, part_hi,
-                                          part_lo, mom);
-    else
-      node_moments<FOREST, REFRESH, DEEP>(c, lv & 31, c_pbeg[c], c_first[c], min(max(c_nch[c], 0), 8), K, offs,
-                                          S, frame, framef, mom);
+    // the cell's table entries, loaded together
+    const int lv = c_level[c], pbeg = c_pbeg[c], pend = c_pend[c], first = c_first[c], nch = c_nch[c];
+    cell_moments<FOREST, REFRESH, DEEP>(c, lv & 31, (lv & 32) != 0, pbeg, pend, first, min(max(nch, 0), 8), K, offs,
+                                        S, frame, framef, part_hi, part_lo, mom);
   }
 }
 
