@@ -505,6 +505,8 @@ __global__ void __launch_bounds__(kBlock) k_move_state(const uint32_t *__restric
 
 // ---------------------------------------------------------------- cells
 constexpr int kHalo = kMaxCrit;  // >= N_crit >= N_leaf
+constexpr int kLvIpt = 4;        // bodies per thread of the level pass
+constexpr int kLvTile = kBlock * kLvIpt;
 
 // Per body: first level it starts a cell at (common prefix with the previous
 // key + 1), its leaf level, whether it starts a group; per warp: how many
@@ -516,23 +518,23 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
                                                    const int32_t *__restrict__ offs, int S, int n_leaf, int n_crit,
                                                    uint8_t *lohi, uint8_t *gstart, uint32_t *rowcnt, int W) {
   const int DD = DEEP ? D : kLevels;
-  __shared__ uint64_t s_key[kBlock + 2 * kHalo];
-  __shared__ uint64_t s_klo[DEEP ? kBlock + 2 * kHalo : 1];
+  __shared__ uint64_t s_key[kLvTile + 2 * kHalo];
+  __shared__ uint64_t s_klo[DEEP ? kLvTile + 2 * kHalo : 1];
   // common prefix (levels) of the keys at shared positions a and b
   auto lcp = [&](int a, int b) -> int {
     return DEEP ? key_lcp2(s_key[a], s_klo[a], s_key[b], s_klo[b], DD) : key_lcp(s_key[a], s_key[b]);
   };
-  __shared__ int8_t s_wl[kBlock + kHalo];  // lcp of windows of N_leaf + 1 keys starting at b0 - kHalo + t
-  __shared__ int8_t s_wc[kBlock + kHalo];  // lcp of windows of N_crit + 1 keys
-  __shared__ int8_t s_tl[kBlock + kHalo], s_tc[kBlock + kHalo];  // doubling buffers
-  const int b0 = blockIdx.x * kBlock;
-  for (int t = threadIdx.x; t < kBlock + 2 * kHalo; t += kBlock) {
+  __shared__ int8_t s_wl[kLvTile + kHalo];  // lcp of windows of N_leaf + 1 keys starting at b0 - kHalo + t
+  __shared__ int8_t s_wc[kLvTile + kHalo];  // lcp of windows of N_crit + 1 keys
+  __shared__ int8_t s_tl[kLvTile + kHalo], s_tc[kLvTile + kHalo];  // doubling buffers
+  const int b0 = blockIdx.x * kLvTile;
+  for (int t = threadIdx.x; t < kLvTile + 2 * kHalo; t += kBlock) {
     int i = b0 - kHalo + t;
     s_key[t] = (i >= 0 && i < n) ? skey[i] : 0;
     if (DEEP) s_klo[t] = (i >= 0 && i < n) ? skey_lo[i] : 0;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < kBlock + kHalo; t += kBlock) {
+  for (int t = threadIdx.x; t < kLvTile + kHalo; t += kBlock) {
     int s0 = b0 - kHalo + t;  // window start
     int8_t wl = -1, wc = -1;
     if (s0 >= 0 && s0 < n) {
@@ -553,7 +555,7 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
   // the largest lcp over the N + 1 windows holding a body is a sliding maximum
   // of fixed length: one sparse-table level T[x] = max(w[x .. x + 2^j - 1]),
   // j = floor(log2(N + 1)), built by j doublings, answers it with two reads
-  const int len = kBlock + kHalo;
+  const int len = kLvTile + kHalo;
   const int jl = 31 - __clz(n_leaf + 1), jc = 31 - __clz(n_crit + 1);
   int8_t *al = s_wl, *bl = s_tl, *ac = s_wc, *bc = s_tc;
   for (int m = 0; m < max(jl, jc); ++m) {
@@ -574,51 +576,55 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
       bc = x;
     }
   }
-  const int i = b0 + threadIdx.x;
-  const bool ok = i < n;
-  int lo = 1, hi = 0, gs = 0;
-  if (ok) {
-    int sb = 0;
-    if (FOREST) sb = offs[sys_of(offs, S, i)];
-    const int t = threadIdx.x + kHalo;  // position of i in s_key
-    int prev = (i > sb) ? lcp(t - 1, t) : -1;
-    // windows of N+1 keys starting at i-N .. i (a window's lcp is -1 where it
-    // leaves the system, so windows starting before the system's first body count nothing)
-    const int wl = max((int)al[t - n_leaf], (int)al[t + 1 - (1 << jl)]);
-    const int wc = max((int)ac[t - n_crit], (int)ac[t + 1 - (1 << jc)]);
-    int lam = min(wl + 1, DD);
-    int mu = wc + 1;  // D + 1: even the level-D cell holds more than N_crit bodies
-    lo = prev + 1;
-    hi = lam;
-    if (mu <= lam) {
-      gs = (lo <= mu);
-    } else {
-      // chunks of N_crit inside a level-D leaf: find the start of the run of equal keys
-      const uint64_t kk = s_key[t], kl = DEEP ? s_klo[t] : 0;
-      int a = sb, b = i;  // first index in [a, b] with key == (kk, kl)
-      while (a < b) {
-        int mid = (a + b) >> 1;
-        const uint64_t h = skey[mid];
-        if (h < kk || (DEEP && h == kk && skey_lo[mid] < kl)) a = mid + 1; else b = mid;
+  // each thread takes bodies j kBlock + threadIdx.x, j < kLvIpt: a warp holds 32
+  // consecutive bodies, the unit of the per-warp counts
+  for (int j = 0; j < kLvIpt; ++j) {
+    const int i = b0 + j * kBlock + threadIdx.x;
+    const bool ok = i < n;
+    int lo = 1, hi = 0, gs = 0;
+    if (ok) {
+      int sb = 0;
+      if (FOREST) sb = offs[sys_of(offs, S, i)];
+      const int t = j * kBlock + threadIdx.x + kHalo;  // position of i in s_key
+      int prev = (i > sb) ? lcp(t - 1, t) : -1;
+      // windows of N+1 keys starting at i-N .. i (a window's lcp is -1 where it
+      // leaves the system, so windows starting before the system's first body count nothing)
+      const int wl = max((int)al[t - n_leaf], (int)al[t + 1 - (1 << jl)]);
+      const int wc = max((int)ac[t - n_crit], (int)ac[t + 1 - (1 << jc)]);
+      int lam = min(wl + 1, DD);
+      int mu = wc + 1;  // D + 1: even the level-D cell holds more than N_crit bodies
+      lo = prev + 1;
+      hi = lam;
+      if (mu <= lam) {
+        gs = (lo <= mu);
+      } else {
+        // chunks of N_crit inside a level-D leaf: find the start of the run of equal keys
+        const uint64_t kk = s_key[t], kl = DEEP ? s_klo[t] : 0;
+        int a = sb, b = i;  // first index in [a, b] with key == (kk, kl)
+        while (a < b) {
+          int mid = (a + b) >> 1;
+          const uint64_t h = skey[mid];
+          if (h < kk || (DEEP && h == kk && skey_lo[mid] < kl)) a = mid + 1; else b = mid;
+        }
+        gs = ((i - a) % n_crit) == 0;
       }
-      gs = ((i - a) % n_crit) == 0;
+      lohi[2 * (size_t)i] = (uint8_t)lo;
+      lohi[2 * (size_t)i + 1] = (uint8_t)hi;
+      gstart[i] = (uint8_t)gs;
     }
-    lohi[2 * (size_t)i] = (uint8_t)lo;
-    lohi[2 * (size_t)i + 1] = (uint8_t)hi;
-    gstart[i] = (uint8_t)gs;
-  }
-  const int lane = threadIdx.x & 31;
-  const int w = i >> 5;
-  uint32_t mine = 0;
+    const int lane = threadIdx.x & 31;
+    const int w = i >> 5;
+    uint32_t mine = 0;
 #pragma unroll
-  for (int k = 0; k <= (DEEP ? kLevelsMax : kLevels); ++k) {
-    if (DEEP && k > DD) break;
-    unsigned b = __ballot_sync(kFull, ok && lo <= k && k <= hi);
-    if (lane == k) mine = __popc(b);
+    for (int k = 0; k <= (DEEP ? kLevelsMax : kLevels); ++k) {
+      if (DEEP && k > DD) break;
+      unsigned b = __ballot_sync(kFull, ok && lo <= k && k <= hi);
+      if (lane == k) mine = __popc(b);
+    }
+    unsigned bg = __ballot_sync(kFull, ok && gs);
+    if (lane == DD + 1) mine = __popc(bg);  // rows 0..D: cells per level; row D + 1: groups
+    if (lane < DD + 2 && w < W) rowcnt[(size_t)lane * W + w] = mine;
   }
-  unsigned bg = __ballot_sync(kFull, ok && gs);
-  if (lane == DD + 1) mine = __popc(bg);  // rows 0..D: cells per level; row D + 1: groups
-  if (lane < DD + 2 && w < W) rowcnt[(size_t)lane * W + w] = mine;
 }
 
 // Writes every cell (level, leaf flag, first body, parent/first child where
@@ -645,21 +651,29 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
   const int DD = DEEP ? D : kLevels;
   const uint32_t C = rowoff[(size_t)(DD + 1) * W];
   int prev = -1;
+  unsigned pb = 0;  // which lanes started a cell one level up
   for (int k = 0; k <= DD; ++k) {
     bool in = ok && lo <= k && k <= hi;
     unsigned b = __ballot_sync(kFull, in);
-    if (b == 0) continue;
     if (in) {
       int cell = (int)(rowoff[(size_t)k * W + w] + __popc(b & lt));
       bool leaf = (k == hi);
       c_level[cell] = k | (leaf ? 32 : 0);
       c_pbeg[cell] = i;
-      c_parent[cell] = (k > lo) ? prev : -1;
+      // parent: the cell this body started one level up, or else the last
+      // level-(k-1) cell started before this body (the one holding it, as
+      // cells of a level are in body order and nest): the last such start
+      // in this warp's lower lanes, or the last one of the earlier warps
+      int par = -1;
+      if (k > lo) par = prev;
+      else if (k > 0) par = (int)(rowoff[(size_t)(k - 1) * W + w] + __popc(pb & lt)) - 1;
+      c_parent[cell] = par;
       c_first[cell] = -1;
       if (k > lo) c_first[prev] = cell;
       if (k == 0) sys_root[s] = cell;
       prev = cell;
     }
+    pb = b;
   }
   unsigned bg = __ballot_sync(kFull, ok && gs);
   if (ok && gs) {
@@ -675,18 +689,19 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
   }
 }
 
-// One thread per cell: body range end (galloping search in the sorted keys),
-// parent (binary search among the cells one level up), number of children
-// (binary search among the cells one level down) and the walk's link word.
+// One thread per cell: body range end (galloping search in the sorted keys)
+// and, for a leaf, its link word.  A node's children are the cells one
+// level down with it as parent, consecutive; the last of them writes the
+// node's child count and link word.
 template <bool FOREST, bool DEEP>
 __global__ void __launch_bounds__(kBlock) k_link(int n, const uint64_t *__restrict__ skey,
                                                  const uint64_t *__restrict__ skey_lo, int D,
                                                  const int32_t *__restrict__ offs, int S,
-                                                 const uint32_t *__restrict__ rowoff, int W,
-                                                 const int32_t *__restrict__ counts, int32_t *c_level,
+                                                 const int32_t *__restrict__ counts,
+                                                 const int32_t *__restrict__ c_level,
                                                  const int32_t *__restrict__ c_pbeg, int32_t *c_pend,
-                                                 int32_t *c_parent, const int32_t *__restrict__ c_first,
-                                                 int32_t *c_nch, int2 *c_link) {
+                                                 const int32_t *__restrict__ c_parent,
+                                                 const int32_t *__restrict__ c_first, int32_t *c_nch, int2 *c_link) {
   const int C = counts[0];
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     const int lv = c_level[c];
@@ -717,30 +732,18 @@ __global__ void __launch_bounds__(kBlock) k_link(int n, const uint64_t *__restri
       pend = a;
     }
     c_pend[c] = pend;
-    int par = c_parent[c];
-    if (k > 0 && par < 0) {
-      int a = (int)rowoff[(size_t)(k - 1) * W], b = (int)rowoff[(size_t)k * W] - 1;  // last cell with pbeg <= i
-      while (a < b) {
-        int mid = (a + b + 1) >> 1;
-        if (c_pbeg[mid] <= i) a = mid; else b = mid - 1;
-      }
-      par = a;
-      c_parent[c] = par;
-    }
-    int nch = 0;
-    if (!leaf) {
-      const int f = c_first[c];
-      int a = f, b = (int)rowoff[(size_t)(k + 2) * W];  // first level-(k+1) cell with pbeg >= pend
-      while (a < b) {
-        int mid = (a + b) >> 1;
-        if (c_pbeg[mid] < pend) a = mid + 1; else b = mid;
-      }
-      nch = a - f;
-      c_link[c] = make_int2(f, nch);
-    } else {
+    if (leaf) {
+      c_nch[c] = 0;
       c_link[c] = make_int2(i, (int)((unsigned)(pend - i) | 0x80000000u));
     }
-    c_nch[c] = nch;
+    if (k > 0) {
+      const int par = c_parent[c];
+      if (c + 1 >= C || c_parent[c + 1] != par) {
+        const int f = c_first[par], nch = c - f + 1;
+        c_nch[par] = nch;
+        c_link[par] = make_int2(f, nch);
+      }
+    }
   }
 }
 
@@ -1008,7 +1011,7 @@ static cudaError_t cells_impl(Ctx &c, cudaStream_t s) {
   const int n = (int)c.n, D = c.levels;
   const int W = cdiv(n, 32);
   const int nb = cdiv(n, kBlock);
-  k_levels<FOREST, DEEP><<<nb, kBlock, 0, s>>>(c.key[0], c.skey_lo, D, n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit,
+  k_levels<FOREST, DEEP><<<cdiv(n, kLvTile), kBlock, 0, s>>>(c.key[0], c.skey_lo, D, n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit,
                                                c.lohi, c.gstart, c.rowcnt, W);
   c.launches++;
   cudaError_t e = launch_scan_u32(c, c.rowcnt, c.rowoff, (int64_t)(D + 2) * W, s);
@@ -1016,9 +1019,9 @@ static cudaError_t cells_impl(Ctx &c, cudaStream_t s) {
   k_emit<FOREST, DEEP><<<nb, kBlock, 0, s>>>(n, D, c.offs, c.n_sys, c.lohi, c.gstart, c.rowoff, W, c.scan_total,
                                              c.c_level, c.c_pbeg, c.c_parent, c.c_first, c.sys_root,
                                              c.g_beg, c.g_sys, c.d_counts);
-  k_link<FOREST, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(n, c.key[0], c.skey_lo, D, c.offs, c.n_sys, c.rowoff, W,
-                                                        c.d_counts, c.c_level, c.c_pbeg, c.c_pend, c.c_parent,
-                                                        c.c_first, c.c_nch, c.c_link);
+  k_link<FOREST, DEEP><<<c.num_sms * 8, kBlock, 0, s>>>(n, c.key[0], c.skey_lo, D, c.offs, c.n_sys, c.d_counts,
+                                                        c.c_level, c.c_pbeg, c.c_pend, c.c_parent, c.c_first,
+                                                        c.c_nch, c.c_link);
   c.launches += 2;
   return cudaGetLastError();
 }
