@@ -190,6 +190,10 @@ void record(Ctx &c, cudaEvent_t e, cudaStream_t s) {
   else cudaEventRecord(e, s);
 }
 
+// Event slot of the leapfrog's predict (drift) kernel; phase 6 reports it
+// with the correct (kick) kernel.
+constexpr int kPhasePredict = BH_NPHASES;
+
 struct Phase {
   Ctx &c;
   cudaStream_t s;
@@ -297,7 +301,7 @@ int step_impl(Ctx &c, double dt, float theta, float eps, bool init, cudaStream_t
   c.split_open = false;  // a whole step ends any step in parts
   if (c.n == 0) return BH_OK;
   if (!init) {
-    Phase ph(c, s, 6);
+    Phase ph(c, s, kPhasePredict);
     if ((e = bh::launch_predict(c, dt, s))) return cu(e);
   }
   const int a = c.state_cur;
@@ -434,7 +438,7 @@ static int build_common(bh_ctx *ctx, const double *pos, const double *mass, int6
   c.have_state = c.have_acc = false;
   c.block_on = c.block_tree = false;
   drop_graphs(c);
-  for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
+  for (int i = 0; i <= BH_NPHASES; ++i) c.phase_rec[i] = false;
   if (c.profiling) cudaEventRecord(c.ev[7][0], s);
   if (n == 0) {
     rc = cu(cudaMemsetAsync(c.d_counts, 0, 4 * sizeof(int32_t), s));
@@ -472,7 +476,7 @@ int bh_compute_forces(bh_ctx *ctx, float theta, float eps, float *acc, float *po
   DeviceGuard g(c.device);
   cudaStream_t s = (cudaStream_t)stream;
   if (c.profiling) cudaEventRecord(c.ev[7][0], s);
-  for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
+  for (int i = 0; i <= BH_NPHASES; ++i) c.phase_rec[i] = false;
   rc = walk_phase(c, theta, eps, bh::kOutCaller, acc, pot, s);
   if (c.profiling) {
     cudaEventRecord(c.ev[7][1], s);
@@ -556,7 +560,7 @@ int bh_step(bh_ctx *ctx, double dt, float theta, float eps, void *stream) {
   DeviceGuard g(c.device);
   cudaStream_t s = (cudaStream_t)stream;
   c.block_on = c.block_tree = false;  // a shared step moves every body by dt
-  for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
+  for (int i = 0; i <= BH_NPHASES; ++i) c.phase_rec[i] = false;
   if (c.profiling) cudaEventRecord(c.ev[7][0], s);
   if (!c.have_acc) {
     rc = step_impl(c, 0.0, theta, eps, true, s);
@@ -642,7 +646,7 @@ int bh_step_begin(bh_ctx *ctx, double dt, int32_t init, void *stream) {
   }
   cudaError_t e;
   if (!init) {
-    Phase ph(c, s, 6);
+    Phase ph(c, s, kPhasePredict);
     if ((e = bh::launch_predict(c, dt, s))) return cu(e);
   }
   const int a = c.state_cur;
@@ -740,12 +744,12 @@ int bh_block_step(bh_ctx *ctx, float theta, float eps, int32_t rebuild, void *st
   DeviceGuard g(c.device);
   cudaStream_t s = (cudaStream_t)stream;
   drop_graphs(c);
-  for (int i = 0; i < BH_NPHASES; ++i) c.phase_rec[i] = false;
+  for (int i = 0; i <= BH_NPHASES; ++i) c.phase_rec[i] = false;
   if (c.profiling) cudaEventRecord(c.ev[7][0], s);
   const bool full = rebuild || !c.block_tree;
   cudaError_t e;
   {
-    Phase ph(c, s, 6);
+    Phase ph(c, s, kPhasePredict);
     if ((e = bh::launch_block_predict(c, s))) return cu(e);
   }
   if (full) {
@@ -1005,15 +1009,19 @@ int bh_phase_times(bh_ctx *ctx, float ms[BH_NPHASES]) {
   if (!ctx || !ms) return BH_ERR_INVALID_ARG;
   Ctx &c = ctx->c;
   DeviceGuard g(c.device);
-  for (int i = 0; i < BH_NPHASES; ++i) {
-    ms[i] = 0.f;
+  // slot BH_NPHASES holds the predict half of the leapfrog, reported in phase 6
+  float t[BH_NPHASES + 1];
+  for (int i = 0; i <= BH_NPHASES; ++i) {
+    t[i] = 0.f;
     if (!c.phase_rec[i]) continue;
     if (cudaEventSynchronize(c.ev[i][1]) != cudaSuccess) return BH_ERR_CUDA;
-    if (cudaEventElapsedTime(&ms[i], c.ev[i][0], c.ev[i][1]) != cudaSuccess) {
-      ms[i] = 0.f;
+    if (cudaEventElapsedTime(&t[i], c.ev[i][0], c.ev[i][1]) != cudaSuccess) {
+      t[i] = 0.f;
       cudaGetLastError();  // do not leave the failed query for the next launch check
     }
   }
+  for (int i = 0; i < BH_NPHASES; ++i) ms[i] = t[i];
+  ms[6] += t[kPhasePredict];
   return BH_OK;
 }
 

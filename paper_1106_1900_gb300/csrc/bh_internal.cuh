@@ -136,7 +136,7 @@ struct Ctx {
   bool capturing = false;
   cudaEvent_t ev[BH_NPHASES + 1][2] = {};
   float phase_ms[BH_NPHASES] = {};
-  bool phase_rec[BH_NPHASES] = {};
+  bool phase_rec[BH_NPHASES + 1] = {};
   cudaStream_t cap_stream = nullptr;
   // one captured step per state-buffer parity (the state swaps buffers every step)
   cudaGraph_t graph[2] = {nullptr, nullptr};

@@ -235,8 +235,9 @@ __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos,
 }
 
 // ----------------------------------------------------------------- sort
+constexpr int kSortThreads = 256;  // threads of a digit pass (the first 256 also own one digit each)
 constexpr int kSortIpt = 8;
-constexpr int kSortTile = kBlock * kSortIpt;
+constexpr int kSortTile = kSortThreads * kSortIpt;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookback = 8;  // predecessor tiles read per look-back step
@@ -293,15 +294,17 @@ __global__ void k_sort_binscan(uint32_t *hist) {
   h[threadIdx.x] = s[threadIdx.x];
 }
 
-// 256-thread exclusive scan helper; returns the exclusive prefix of v.
-__device__ __forceinline__ uint32_t block256_exclusive(uint32_t v, uint32_t *s_warp) {
+// Exclusive scan of the 256 digit values held by threads 0..255 (the other
+// threads pass 0 and take part only in the barriers); returns the exclusive
+// prefix of v.
+__device__ __forceinline__ uint32_t digit_exclusive(uint32_t v, uint32_t *s_warp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = v;
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t y = __shfl_up_sync(kFull, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) s_warp[warp] = x;
+  if (lane == 31 && warp < 8) s_warp[warp] = x;
   __syncthreads();
   if (warp == 0) {
     uint32_t w = (lane < 8) ? s_warp[lane] : 0;
@@ -312,7 +315,7 @@ __device__ __forceinline__ uint32_t block256_exclusive(uint32_t v, uint32_t *s_w
     if (lane < 8) s_warp[lane] = w;
   }
   __syncthreads();
-  uint32_t before = (warp > 0) ? s_warp[warp - 1] : 0;
+  uint32_t before = (warp > 0 && warp < 8) ? s_warp[warp - 1] : 0;
   __syncthreads();
   return before + x - v;
 }
@@ -320,13 +323,11 @@ __device__ __forceinline__ uint32_t block256_exclusive(uint32_t v, uint32_t *s_w
 // One stable digit pass.  Tiles are taken in launch order from a counter, so
 // every tile's predecessors are already running; each tile publishes its
 // digit counts, then sums its predecessors' (bounded wait), then scatters.
-__global__ void __launch_bounds__(kBlock, 4) k_sort_pass(const uint64_t *__restrict__ kin,
-                                                      const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                                                      uint32_t *__restrict__ vout, int n, int byte,
-                                                      const uint32_t *__restrict__ binbase, uint32_t *status,
-                                                      uint32_t *tile_ctr, const int32_t *__restrict__ offs, int S,
-                                                      int32_t *err) {
-  __shared__ uint32_t s_wcnt[kBlock / 32][256];
+__global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads)
+    k_sort_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+                uint32_t *__restrict__ vout, int n, int byte, const uint32_t *__restrict__ binbase,
+                uint32_t *status, uint32_t *tile_ctr, const int32_t *__restrict__ offs, int S, int32_t *err) {
+  __shared__ uint32_t s_wcnt[kSortThreads / 32][256];
   __shared__ uint32_t s_tstart[256];
   __shared__ uint32_t s_gbase[256];
   __shared__ uint32_t s_scan[8];
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sort_pass(const uint64_t *__restr
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  for (int t = threadIdx.x; t < (kBlock / 32) * 256; t += kBlock) (&s_wcnt[0][0])[t] = 0;
+  for (int t = threadIdx.x; t < (kSortThreads / 32) * 256; t += kSortThreads) (&s_wcnt[0][0])[t] = 0;
   __syncthreads();
   const uint32_t tile = s_tile;
   const int base = (int)tile * kSortTile;
@@ -365,56 +366,59 @@ __global__ void __launch_bounds__(kBlock, 4) k_sort_pass(const uint64_t *__restr
     __syncwarp();
   }
   __syncthreads();
-  // digit t: per-warp exclusive offsets and the tile's count
+  // digit t (threads 0..255): per-warp exclusive offsets and the tile's count
   const int t = threadIdx.x;
+  const bool dig = t < 256;
   uint32_t tot = 0;
-  for (int w = 0; w < kBlock / 32; ++w) {
-    uint32_t c = s_wcnt[w][t];
-    s_wcnt[w][t] = tot;
-    tot += c;
-  }
-  uint32_t *my = status + (size_t)tile * 256;
-  if (tile == 0) atomicExch(&my[t], kFlagInc | tot);
-  else atomicExch(&my[t], kFlagAgg | tot);
-  uint32_t tstart = block256_exclusive(tot, s_scan);
-  s_tstart[t] = tstart;
-  uint32_t excl = 0;
-  if (tile > 0) {
-    // decoupled look-back, kLookback predecessors per step: their status
-    // words are loaded together, then summed from the nearest back to the
-    // first inclusive prefix; an unpublished one stops the step and is
-    // polled again (tile 0 is always inclusive, so the walk ends)
-    int pr = (int)tile - 1;
-    int spins = 0;
-    while (pr >= 0) {
-      uint32_t w[kLookback];
-#pragma unroll
-      for (int q = 0; q < kLookback; ++q)
-        w[q] = (pr - q >= 0) ? __ldcv(&status[(size_t)(pr - q) * 256 + t]) : kFlagInc;
-      int q = 0;
-      bool found = false;
-      for (; q < kLookback; ++q) {
-        const uint32_t f = w[q] & ~kValMask;
-        if (f == 0) break;
-        excl += w[q] & kValMask;
-        if (f == kFlagInc) {
-          found = true;
-          break;
-        }
-      }
-      if (found) break;
-      if (q == 0) {
-        if (++spins > kSpinLimit) {
-          set_status(err, BH_ERR_TIMEOUT);
-          break;
-        }
-        __nanosleep(32);
-      }
-      pr -= q;
+  if (dig)
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      uint32_t c = s_wcnt[w][t];
+      s_wcnt[w][t] = tot;
+      tot += c;
     }
-    atomicExch(&my[t], kFlagInc | (excl + tot));
+  uint32_t *my = status + (size_t)tile * 256;
+  if (dig) atomicExch(&my[t], (tile == 0 ? kFlagInc : kFlagAgg) | tot);
+  uint32_t tstart = digit_exclusive(dig ? tot : 0u, s_scan);
+  if (dig) {
+    s_tstart[t] = tstart;
+    uint32_t excl = 0;
+    if (tile > 0) {
+      // decoupled look-back, kLookback predecessors per step: their status
+      // words are loaded together, then summed from the nearest back to the
+      // first inclusive prefix; an unpublished one stops the step and is
+      // polled again (tile 0 is always inclusive, so the walk ends)
+      int pr = (int)tile - 1;
+      int spins = 0;
+      while (pr >= 0) {
+        uint32_t w[kLookback];
+#pragma unroll
+        for (int q = 0; q < kLookback; ++q)
+          w[q] = (pr - q >= 0) ? __ldcv(&status[(size_t)(pr - q) * 256 + t]) : kFlagInc;
+        int q = 0;
+        bool found = false;
+        for (; q < kLookback; ++q) {
+          const uint32_t f = w[q] & ~kValMask;
+          if (f == 0) break;
+          excl += w[q] & kValMask;
+          if (f == kFlagInc) {
+            found = true;
+            break;
+          }
+        }
+        if (found) break;
+        if (q == 0) {
+          if (++spins > kSpinLimit) {
+            set_status(err, BH_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(32);
+        }
+        pr -= q;
+      }
+      atomicExch(&my[t], kFlagInc | (excl + tot));
+    }
+    s_gbase[t] = binbase[t] + excl;
   }
-  s_gbase[t] = binbase[t] + excl;
   __syncthreads();
   // scatter into shared memory in (digit, arrival) order
 #pragma unroll
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_sort_pass(const uint64_t *__restr
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < tile_n; e += kBlock) {
+  for (int e = threadIdx.x; e < tile_n; e += kSortThreads) {
     uint32_t dd = s_d[e];
     uint32_t g = s_gbase[dd] + ((uint32_t)e - s_tstart[dd]);
     kout[g] = s_k[e];
@@ -932,7 +936,7 @@ cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
       k_gather_key<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.idx[src], c.key_hi0, c.key[src], n);
       c.launches++;
     }
-    k_sort_pass<<<tiles, kBlock, dyn, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1], n,
+    k_sort_pass<<<tiles, kSortThreads, dyn, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1], n,
                                            pass_byte(p, lo_passes), c.sort_hist + p * 256,
                                            c.sort_status + (size_t)p * tiles * 256, c.sort_tile_ctr + p, c.offs,
                                            c.n_sys, c.d_status);
