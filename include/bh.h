@@ -314,6 +314,18 @@ int bh_walk_time(bh_ctx *ctx, float *ms);
 int bh_prim_exclusive_scan(bh_ctx *ctx, const uint32_t *in_dev, uint32_t *out_dev, int64_t n, uint64_t *total_host,
                            void *stream);
 
+/* The precision split of §3.2's reading (FP64 state, FP32 arithmetic in
+ * cell-relative coordinates), exposed for verification: for i < n,
+ * hi_dev[i] = x_dev[i] rounded to the nearest float (ties to even),
+ * lo_dev[i] = x_dev[i] - hi_dev[i] (exact in FP64) rounded the same way, and
+ * wide_dev[i] = f_dev[i] converted exactly to FP64 -- the conversions every
+ * step applies to each body, done on the integer units.  All pointers are
+ * device buffers of n elements owned by the caller.  No context needed;
+ * stream-ordered, asynchronous.  Returns BH_ERR_INVALID_ARG for n < 0,
+ * n >= 2^31 or a null pointer with n > 0, BH_ERR_CUDA if the launch fails. */
+int bh_prim_split2(const double *x_dev, const float *f_dev, int64_t n, float *hi_dev, float *lo_dev,
+                   double *wide_dev, void *stream);
+
 /* Direct summation (§4.2.1 measures the tree's error against it; §3.3: theta
  * -> 0 turns the tree-code into it): acceleration and potential on each listed
  * target from every other body, softened like the particle-particle term.

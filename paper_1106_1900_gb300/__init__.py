@@ -155,6 +155,8 @@ _SIG = {
     "bh_fp32_peak_probe": [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p],
     "bh_exclusive_scan_noalloc": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_void_p],
+    "bh_prim_split2": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                       ctypes.c_void_p, ctypes.c_void_p],
     "bh_direct_forces": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                          ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
 }
@@ -261,6 +263,25 @@ def direct_forces(pos, mass, targets, eps: float, stream=None):
     _check(load().bh_direct_forces(_ptr(pos), _ptr(mass), pos.shape[0], _ptr(targets), nt, float(eps), _ptr(acc),
                                    _ptr(pot), _stream(stream)), "bh_direct_forces")
     return acc, pot
+
+
+def split2(x, f, stream=None):
+    """The step kernels' conversions element by element through
+    ``bh_prim_split2``: (hi, lo) floats of the FP64 tensor ``x`` (hi = x
+    rounded, lo = the rest rounded) and the FP64 widening of the float32
+    tensor ``f`` (same length, both contiguous CUDA tensors)."""
+    import torch
+
+    px = _arg(x, torch.float64, "x")
+    pf = _arg(f, torch.float32, "f")
+    if x.numel() != f.numel():
+        raise ValueError("x and f must have the same length")
+    hi = torch.empty(x.numel(), dtype=torch.float32, device=x.device)
+    lo = torch.empty_like(hi)
+    wide = torch.empty(x.numel(), dtype=torch.float64, device=x.device)
+    _check(load().bh_prim_split2(px, pf, x.numel(), _ptr(hi), _ptr(lo), _ptr(wide), _stream(stream)),
+           "bh_prim_split2")
+    return hi, lo, wide
 
 
 def exclusive_scan_noalloc(x, out=None, total=None, stream=None):

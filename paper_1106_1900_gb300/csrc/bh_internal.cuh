@@ -254,10 +254,58 @@ __device__ __forceinline__ uint32_t compact3(uint64_t x) {
   return (uint32_t)x;
 }
 
-// FP64 value split into two floats: hi = rn(x), lo = rn(x - hi).
+// FP32 <-> FP64 conversions on the integer units.  GB300's FP64 pipe runs
+// at a small fraction of its FP32 rate and executes the hardware
+// conversions too, so the state updates and the two-float splits that
+// convert every body's coordinates were bound by it.  Both are written from
+// the IEEE 754 binary32 / binary64 formats.
+//
+// widen: exact.  A normal number keeps sign and mantissa (moved up 29 bits)
+// and its biased exponent gains 1023 - 127 = 896; a subnormal m 2^-149 is
+// normalised (leading bit p of m: exponent p + 874, mantissa m shifted up
+// 23 - p bits); zeros, infinities and NaNs map to their binary64 forms.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  uint64_t bits = (uint64_t)(u >> 31) << 63;
+  if (e == 0xffu) {
+    bits |= (0x7ffull << 52) | ((uint64_t)m << 29);
+  } else if (e != 0u) {
+    bits |= ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+  } else if (m != 0u) {
+    const uint32_t p = 31u - (uint32_t)__clz((int)m);
+    bits |= ((uint64_t)(p + 874u) << 52) | ((uint64_t)((m << (23u - p)) & 0x7fffffu) << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// narrow_rn: round to nearest, ties to even, for results in the normal
+// binary32 range (biased exponent 897..1150 of the binary64 input): keep the
+// top 23 mantissa bits, and add one unit when the 29 dropped bits exceed
+// half a unit or equal it with an odd last bit (a carry steps the exponent,
+// to infinity past the largest float).  Zeros keep their sign; every other
+// input (subnormal or overflowing results, infinities, NaN) takes the
+// hardware conversion.
+__device__ __forceinline__ float narrow_rn(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  if (e >= 897u && e <= 1150u) {
+    const uint64_t m = b & 0xfffffffffffffull;
+    uint32_t r = ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1fffffffu);
+    if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ++r;
+    return __uint_as_float(sign | r);
+  }
+  if ((b << 1) == 0) return __uint_as_float(sign);
+  return __double2float_rn(x);
+}
+
+// x = hi + lo: hi the float nearest x, lo the float nearest the exact rest
+// x - hi (one FP64 subtraction).
 __device__ __forceinline__ void split2(double x, float &hi, float &lo) {
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(__dsub_rn(x, (double)hi));
+  hi = narrow_rn(x);
+  lo = narrow_rn(__dsub_rn(x, widen(hi)));
 }
 
 }  // namespace bh

@@ -12,13 +12,14 @@ constexpr int kDiagBlocks = 256;
 
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
-// x += v dt + a dt^2/2 ; v_p = v + a dt (old acceleration, FP32 -> FP64)
+// x += v dt + a dt^2/2 ; v_p = v + a dt (old acceleration, FP32 -> FP64 by
+// widen(): the conversions stay off the FP64 pipe, the update's bound)
 __global__ void __launch_bounds__(kBlock) k_predict(int n, double *x, double *v, const float4 *__restrict__ a,
                                                     double dt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 ai = a[i];
-  double ac[3] = {(double)ai.x, (double)ai.y, (double)ai.z};
+  double ac[3] = {widen(ai.x), widen(ai.y), widen(ai.z)};
   double hdt2 = 0.5 * dt * dt;
   for (int d = 0; d < 3; ++d) {
     size_t k = 3 * (size_t)i + d;
@@ -35,9 +36,9 @@ __global__ void __launch_bounds__(kBlock) k_correct(int n, double *v, float4 *a_
   if (i >= n) return;
   float4 o = a_old[i], w = a_new[i];
   double h = 0.5 * dt;
-  v[3 * (size_t)i] += ((double)w.x - (double)o.x) * h;
-  v[3 * (size_t)i + 1] += ((double)w.y - (double)o.y) * h;
-  v[3 * (size_t)i + 2] += ((double)w.z - (double)o.z) * h;
+  v[3 * (size_t)i] += (widen(w.x) - widen(o.x)) * h;
+  v[3 * (size_t)i + 1] += (widen(w.y) - widen(o.y)) * h;
+  v[3 * (size_t)i + 2] += (widen(w.z) - widen(o.z)) * h;
   a_old[i] = w;
 }
 
@@ -110,6 +111,16 @@ __global__ void k_diag_final(const double *__restrict__ part, int nb, double *ou
   for (int k = 0; k < 5; ++k) out[k] = acc[k];
 }
 
+// The two-float split and the widening the step kernels use, element by
+// element (for verification against IEEE 754 conversions on the host).
+__global__ void __launch_bounds__(kBlock) k_split2(const double *__restrict__ x, const float *__restrict__ f,
+                                                   int n, float *hi, float *lo, double *wide) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  split2(x[i], hi[i], lo[i]);
+  wide[i] = widen(f[i]);
+}
+
 // Eight independent FMA chains per thread; the result is kept live through `sink`.
 __global__ void k_fma_probe(int iters, float *sink) {
   float a0 = threadIdx.x * 1e-7f, a1 = a0 + 1e-7f, a2 = a0 + 2e-7f, a3 = a0 + 3e-7f;
@@ -178,3 +189,13 @@ cudaError_t launch_fma_probe(int blocks, int threads, int iters, float *sink, cu
 }
 
 }  // namespace bh
+
+extern "C" int bh_prim_split2(const double *x_dev, const float *f_dev, int64_t n, float *hi_dev, float *lo_dev,
+                              double *wide_dev, void *stream) {
+  if (n < 0 || n >= (1ll << 31)) return BH_ERR_INVALID_ARG;
+  if (n == 0) return BH_OK;
+  if (!x_dev || !f_dev || !hi_dev || !lo_dev || !wide_dev) return BH_ERR_INVALID_ARG;
+  bh::k_split2<<<bh::cdiv(n, bh::kBlock), bh::kBlock, 0, (cudaStream_t)stream>>>(x_dev, f_dev, (int)n, hi_dev,
+                                                                                 lo_dev, wide_dev);
+  return cudaGetLastError() == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+}
