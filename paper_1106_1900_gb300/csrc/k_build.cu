@@ -236,11 +236,14 @@ __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos,
 
 // ----------------------------------------------------------------- sort
 constexpr int kSortThreads = 256;  // threads of a digit pass (the first 256 also own one digit each)
+constexpr int kSortBlocksPerSm = 3;  // resident blocks of the persistent pass
 constexpr int kSortIpt = 8;
 constexpr int kSortTile = kSortThreads * kSortIpt;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
 constexpr int kLookback = 8;  // predecessor tiles read per look-back step
+// two tile buffers (8-byte keys, 4-byte indices) and one digit byte per key
+constexpr size_t kSortDynSmem = (size_t)kSortTile * (2 * (8 + 4) + 1);
 
 // Digit of a pass: byte `byte` of the key word, or (byte < 0) byte -1 - byte
 // of the body's system id.
@@ -320,122 +323,178 @@ __device__ __forceinline__ uint32_t digit_exclusive(uint32_t v, uint32_t *s_warp
   return before + x - v;
 }
 
-// One stable digit pass.  Tiles are taken in launch order from a counter, so
-// every tile's predecessors are already running; each tile publishes its
-// digit counts, then sums its predecessors' (bounded wait), then scatters.
-__global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads)
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 only); bytes < 16
+// reads that many and fills the rest of the 16 with zeros.
+__device__ __forceinline__ void copy16_async(void *dst_smem, const void *src, uint32_t bytes) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void copy_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// waits until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void copy_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Starts the copy of tile `tile`'s keys and indices into a shared buffer:
+// 16-byte pieces, the ones past n zero-filled (their addresses stay inside
+// the arrays: a piece with no byte to read points at the array's start).
+__device__ __forceinline__ void sort_tile_fetch(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                int n, uint32_t tile, uint64_t *s_kb, uint32_t *s_vb) {
+  const int64_t base = (int64_t)tile * kSortTile;
+  for (int c = threadIdx.x; c < kSortTile / 2; c += kSortThreads) {  // two keys per piece
+    const int64_t e = base + 2 * c;
+    const int64_t left = (int64_t)n - e;
+    const uint32_t bytes = left >= 2 ? 16u : (left == 1 ? 8u : 0u);
+    copy16_async(s_kb + 2 * c, bytes ? (const void *)(kin + e) : (const void *)kin, bytes);
+  }
+  for (int c = threadIdx.x; c < kSortTile / 4; c += kSortThreads) {  // four indices per piece
+    const int64_t e = base + 4 * c;
+    const int64_t left = (int64_t)n - e;
+    const uint32_t bytes = left >= 4 ? 16u : (left > 0 ? (uint32_t)left * 4u : 0u);
+    copy16_async(s_vb + 4 * c, bytes ? (const void *)(vin + e) : (const void *)vin, bytes);
+  }
+}
+
+// One stable digit pass over `tiles` tiles of kSortTile keys.  A persistent
+// block takes tiles in order from a counter (every taken tile's predecessors
+// were taken earlier, by running blocks, so waiting on them ends) and, before
+// working on its tile, takes the next one and starts copying it into its
+// second shared buffer, so that the load of one tile overlaps the work on the
+// other.  Per tile: rank the keys by digit in each warp, publish the tile's
+// digit counts, sum the predecessors' (decoupled look-back, bounded wait),
+// then scatter through shared memory.
+__global__ void __launch_bounds__(kSortThreads, kSortBlocksPerSm)
     k_sort_pass(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                uint32_t *__restrict__ vout, int n, int byte, const uint32_t *__restrict__ binbase,
+                uint32_t *__restrict__ vout, int n, uint32_t tiles, int byte, const uint32_t *__restrict__ binbase,
                 uint32_t *status, uint32_t *tile_ctr, const int32_t *__restrict__ offs, int S, int32_t *err) {
   __shared__ uint32_t s_wcnt[kSortThreads / 32][256];
   __shared__ uint32_t s_tstart[256];
   __shared__ uint32_t s_gbase[256];
   __shared__ uint32_t s_scan[8];
   __shared__ uint32_t s_tile;
-  extern __shared__ unsigned char s_dyn[];
-  uint64_t *s_k = reinterpret_cast<uint64_t *>(s_dyn);
-  uint32_t *s_v = reinterpret_cast<uint32_t *>(s_k + kSortTile);
-  uint8_t *s_d = reinterpret_cast<uint8_t *>(s_v + kSortTile);
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  // two tile buffers (keys, then indices) and the digits of the scatter
+  uint64_t *s_kb0 = reinterpret_cast<uint64_t *>(s_dyn);
+  uint32_t *s_vb0 = reinterpret_cast<uint32_t *>(s_kb0 + kSortTile);
+  uint64_t *s_kb1 = reinterpret_cast<uint64_t *>(s_vb0 + kSortTile);
+  uint32_t *s_vb1 = reinterpret_cast<uint32_t *>(s_kb1 + kSortTile);
+  uint8_t *s_d = reinterpret_cast<uint8_t *>(s_vb1 + kSortTile);
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
-  for (int t = threadIdx.x; t < (kSortThreads / 32) * 256; t += kSortThreads) (&s_wcnt[0][0])[t] = 0;
-  __syncthreads();
-  const uint32_t tile = s_tile;
-  const int base = (int)tile * kSortTile;
-  const int tile_n = min(kSortTile, n - base);
-
-  uint64_t k[kSortIpt];
-  uint32_t v[kSortIpt], d[kSortIpt], r[kSortIpt];
   const unsigned lt = lanemask_lt();
-#pragma unroll
-  for (int j = 0; j < kSortIpt; ++j) {
-    int e = base + warp * 32 * kSortIpt + j * 32 + lane;
-    bool ok = e < n;
-    k[j] = ok ? kin[e] : 0;
-    v[j] = ok ? vin[e] : 0;
-    d[j] = ok ? sort_digit(k[j], v[j], byte, offs, S) : 256u;
-  }
-#pragma unroll
-  for (int j = 0; j < kSortIpt; ++j) {
-    unsigned peers = __match_any_sync(kFull, d[j]);
-    uint32_t cnt = (d[j] < 256) ? s_wcnt[warp][d[j]] : 0;
-    r[j] = cnt + __popc(peers & lt);
-    __syncwarp();
-    if (d[j] < 256 && (peers & lt) == 0) s_wcnt[warp][d[j]] = cnt + __popc(peers);
-    __syncwarp();
-  }
+  if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
   __syncthreads();
-  // digit t (threads 0..255): per-warp exclusive offsets and the tile's count
-  const int t = threadIdx.x;
-  const bool dig = t < 256;
-  uint32_t tot = 0;
-  if (dig)
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      uint32_t c = s_wcnt[w][t];
-      s_wcnt[w][t] = tot;
-      tot += c;
-    }
-  uint32_t *my = status + (size_t)tile * 256;
-  if (dig) atomicExch(&my[t], (tile == 0 ? kFlagInc : kFlagAgg) | tot);
-  uint32_t tstart = digit_exclusive(dig ? tot : 0u, s_scan);
-  if (dig) {
-    s_tstart[t] = tstart;
-    uint32_t excl = 0;
-    if (tile > 0) {
-      // decoupled look-back, kLookback predecessors per step: their status
-      // words are loaded together, then summed from the nearest back to the
-      // first inclusive prefix; an unpublished one stops the step and is
-      // polled again (tile 0 is always inclusive, so the walk ends)
-      int pr = (int)tile - 1;
-      int spins = 0;
-      while (pr >= 0) {
-        uint32_t w[kLookback];
+  uint32_t tile = s_tile;
+  if (tile < tiles) sort_tile_fetch(kin, vin, n, tile, s_kb0, s_vb0);
+  copy_async_commit();
+  int buf = 0;
+  while (tile < tiles) {
+    uint64_t *s_kb = buf ? s_kb1 : s_kb0;
+    uint32_t *s_vb = buf ? s_vb1 : s_vb0;
+    __syncthreads();  // everyone has read s_tile and is done with the other buffer
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int t = threadIdx.x; t < (kSortThreads / 32) * 256; t += kSortThreads) (&s_wcnt[0][0])[t] = 0;
+    __syncthreads();
+    const uint32_t next = s_tile;
+    if (next < tiles) sort_tile_fetch(kin, vin, n, next, buf ? s_kb0 : s_kb1, buf ? s_vb0 : s_vb1);
+    copy_async_commit();
+    copy_async_wait_one();  // this thread's pieces of the current tile have landed
+    __syncthreads();        // and everyone's
+    const int base = (int)tile * kSortTile;
+    const int tile_n = min(kSortTile, n - base);
+
+    uint64_t k[kSortIpt];
+    uint32_t v[kSortIpt], d[kSortIpt], r[kSortIpt];
 #pragma unroll
-        for (int q = 0; q < kLookback; ++q)
-          w[q] = (pr - q >= 0) ? __ldcv(&status[(size_t)(pr - q) * 256 + t]) : kFlagInc;
-        int q = 0;
-        bool found = false;
-        for (; q < kLookback; ++q) {
-          const uint32_t f = w[q] & ~kValMask;
-          if (f == 0) break;
-          excl += w[q] & kValMask;
-          if (f == kFlagInc) {
-            found = true;
-            break;
-          }
-        }
-        if (found) break;
-        if (q == 0) {
-          if (++spins > kSpinLimit) {
-            set_status(err, BH_ERR_TIMEOUT);
-            break;
-          }
-          __nanosleep(32);
-        }
-        pr -= q;
+    for (int j = 0; j < kSortIpt; ++j) {
+      const int le = warp * 32 * kSortIpt + j * 32 + lane;
+      const bool ok = le < tile_n;
+      k[j] = s_kb[le];
+      v[j] = s_vb[le];
+      d[j] = ok ? sort_digit(k[j], v[j], byte, offs, S) : 256u;
+    }
+#pragma unroll
+    for (int j = 0; j < kSortIpt; ++j) {
+      unsigned peers = __match_any_sync(kFull, d[j]);
+      uint32_t cnt = (d[j] < 256) ? s_wcnt[warp][d[j]] : 0;
+      r[j] = cnt + __popc(peers & lt);
+      __syncwarp();
+      if (d[j] < 256 && (peers & lt) == 0) s_wcnt[warp][d[j]] = cnt + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // digit t (threads 0..255): per-warp exclusive offsets and the tile's count
+    const int t = threadIdx.x;
+    const bool dig = t < 256;
+    uint32_t tot = 0;
+    if (dig)
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        uint32_t c = s_wcnt[w][t];
+        s_wcnt[w][t] = tot;
+        tot += c;
       }
-      atomicExch(&my[t], kFlagInc | (excl + tot));
-    }
-    s_gbase[t] = binbase[t] + excl;
-  }
-  __syncthreads();
-  // scatter into shared memory in (digit, arrival) order
+    uint32_t *my = status + (size_t)tile * 256;
+    if (dig) atomicExch(&my[t], (tile == 0 ? kFlagInc : kFlagAgg) | tot);
+    uint32_t tstart = digit_exclusive(dig ? tot : 0u, s_scan);
+    if (dig) {
+      s_tstart[t] = tstart;
+      uint32_t excl = 0;
+      if (tile > 0) {
+        // decoupled look-back, kLookback predecessors per step: their status
+        // words are loaded together, then summed from the nearest back to the
+        // first inclusive prefix; an unpublished one stops the step and is
+        // polled again (tile 0 is always inclusive, so the walk ends)
+        int pr = (int)tile - 1;
+        int spins = 0;
+        while (pr >= 0) {
+          uint32_t w[kLookback];
 #pragma unroll
-  for (int j = 0; j < kSortIpt; ++j) {
-    if (d[j] < 256) {
-      uint32_t lp = s_tstart[d[j]] + s_wcnt[warp][d[j]] + r[j];
-      s_k[lp] = k[j];
-      s_v[lp] = v[j];
-      s_d[lp] = (uint8_t)d[j];
+          for (int q = 0; q < kLookback; ++q)
+            w[q] = (pr - q >= 0) ? __ldcv(&status[(size_t)(pr - q) * 256 + t]) : kFlagInc;
+          int q = 0;
+          bool found = false;
+          for (; q < kLookback; ++q) {
+            const uint32_t f = w[q] & ~kValMask;
+            if (f == 0) break;
+            excl += w[q] & kValMask;
+            if (f == kFlagInc) {
+              found = true;
+              break;
+            }
+          }
+          if (found) break;
+          if (q == 0) {
+            if (++spins > kSpinLimit) {
+              set_status(err, BH_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+          pr -= q;
+        }
+        atomicExch(&my[t], kFlagInc | (excl + tot));
+      }
+      s_gbase[t] = binbase[t] + excl;
     }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < tile_n; e += kSortThreads) {
-    uint32_t dd = s_d[e];
-    uint32_t g = s_gbase[dd] + ((uint32_t)e - s_tstart[dd]);
-    kout[g] = s_k[e];
-    vout[g] = s_v[e];
+    __syncthreads();
+    // scatter into the tile's own buffer (its keys are in registers now) in
+    // (digit, arrival) order
+#pragma unroll
+    for (int j = 0; j < kSortIpt; ++j) {
+      if (d[j] < 256) {
+        uint32_t lp = s_tstart[d[j]] + s_wcnt[warp][d[j]] + r[j];
+        s_kb[lp] = k[j];
+        s_vb[lp] = v[j];
+        s_d[lp] = (uint8_t)d[j];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < tile_n; e += kSortThreads) {
+      uint32_t dd = s_d[e];
+      uint32_t g = s_gbase[dd] + ((uint32_t)e - s_tstart[dd]);
+      kout[g] = s_kb[e];
+      vout[g] = s_vb[e];
+    }
+    tile = next;
+    buf ^= 1;
   }
 }
 
@@ -904,9 +963,9 @@ int sort_passes_for(int S, int D) { return sort_lo_passes(D) + 8 + sort_sys_pass
 
 cudaError_t build_init_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)((size_t)kSortTile * (8 + 4 + 1)));
+                                       (int)kSortDynSmem);
   if (e) return e;
-  // four tiles per SM: the largest shared-memory carveout
+  // kSortBlocksPerSm persistent blocks per SM: the largest shared-memory carveout
   return cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 int64_t sort_tiles_for(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
@@ -929,17 +988,17 @@ cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
                                                                    deep ? c.key_hi0 : c.key[0], n, lo_passes, passes,
                                                                    c.offs, c.n_sys, c.sort_hist);
   k_sort_binscan<<<passes, 256, 0, s>>>(c.sort_hist);
-  const size_t dyn = (size_t)kSortTile * (8 + 4 + 1);
+  const int grid = min(tiles, c.num_sms * kSortBlocksPerSm);
   for (int p = 0; p < passes; ++p) {
     int src = p & 1;
     if (deep && p == lo_passes) {  // sorted by the low word: bring the 60-bit word into this order
       k_gather_key<<<cdiv(n, kBlock), kBlock, 0, s>>>(c.idx[src], c.key_hi0, c.key[src], n);
       c.launches++;
     }
-    k_sort_pass<<<tiles, kSortThreads, dyn, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1], n,
-                                           pass_byte(p, lo_passes), c.sort_hist + p * 256,
-                                           c.sort_status + (size_t)p * tiles * 256, c.sort_tile_ctr + p, c.offs,
-                                           c.n_sys, c.d_status);
+    k_sort_pass<<<grid, kSortThreads, kSortDynSmem, s>>>(c.key[src], c.idx[src], c.key[src ^ 1], c.idx[src ^ 1],
+                                                         n, (uint32_t)tiles, pass_byte(p, lo_passes),
+                                                         c.sort_hist + p * 256, c.sort_status + (size_t)p * tiles * 256,
+                                                         c.sort_tile_ctr + p, c.offs, c.n_sys, c.d_status);
   }
   c.launches += 2 + passes;
   if (passes & 1) {  // 9 passes (forest of 2..256 systems): bring the result back to buffer 0
