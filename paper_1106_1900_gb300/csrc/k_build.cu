@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(kBlock) k_keys(const double *__restrict__ pos,
 
 // ----------------------------------------------------------------- sort
 constexpr int kSortThreads = 256;  // threads of a digit pass (the first 256 also own one digit each)
-constexpr int kSortBlocksPerSm = 3;  // resident blocks of the persistent pass
-constexpr int kSortIpt = 8;
+constexpr int kSortBlocksPerSm = 2;  // resident blocks of the persistent pass
+constexpr int kSortIpt = 16;
 constexpr int kSortTile = kSortThreads * kSortIpt;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kValMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 22;
@@ -713,13 +713,19 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
   }
   const int DD = DEEP ? D : kLevels;
   const uint32_t C = rowoff[(size_t)(DD + 1) * W];
+  // this warp's offset in every row (levels 0..D, then groups: at most 32
+  // rows), lane r holding row r, all loaded at once
+  const int lane = threadIdx.x & 31;
+  const uint32_t myoff = (lane <= DD + 1 && w < W) ? rowoff[(size_t)lane * W + w] : 0u;
   int prev = -1;
-  unsigned pb = 0;  // which lanes started a cell one level up
+  unsigned pb = 0;      // which lanes started a cell one level up
+  uint32_t poff = 0;    // this warp's offset one level up
   for (int k = 0; k <= DD; ++k) {
     bool in = ok && lo <= k && k <= hi;
     unsigned b = __ballot_sync(kFull, in);
+    const uint32_t off = __shfl_sync(kFull, myoff, k);
     if (in) {
-      int cell = (int)(rowoff[(size_t)k * W + w] + __popc(b & lt));
+      int cell = (int)(off + __popc(b & lt));
       bool leaf = (k == hi);
       c_level[cell] = k | (leaf ? 32 : 0);
       c_pbeg[cell] = i;
@@ -729,7 +735,7 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
       // in this warp's lower lanes, or the last one of the earlier warps
       int par = -1;
       if (k > lo) par = prev;
-      else if (k > 0) par = (int)(rowoff[(size_t)(k - 1) * W + w] + __popc(pb & lt)) - 1;
+      else if (k > 0) par = (int)(poff + __popc(pb & lt)) - 1;
       c_parent[cell] = par;
       c_first[cell] = -1;
       if (k > lo) c_first[prev] = cell;
@@ -737,10 +743,12 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
       prev = cell;
     }
     pb = b;
+    poff = off;
   }
   unsigned bg = __ballot_sync(kFull, ok && gs);
+  const uint32_t goff = __shfl_sync(kFull, myoff, DD + 1);
   if (ok && gs) {
-    int g = (int)(rowoff[(size_t)(DD + 1) * W + w] - C + __popc(bg & lt));
+    int g = (int)(goff - C + __popc(bg & lt));
     g_beg[g] = i;
     g_sys[g] = s;
   }
