@@ -568,8 +568,12 @@ __global__ void __launch_bounds__(kBlock) k_move_state(const uint32_t *__restric
 
 // ---------------------------------------------------------------- cells
 constexpr int kHalo = kMaxCrit;  // >= N_crit >= N_leaf
-constexpr int kLvIpt = 4;        // bodies per thread of the level pass
-constexpr int kLvTile = kBlock * kLvIpt;
+// bodies per thread of the level pass (deeper keys carry a second key word
+// in shared memory: half as many, to stay within 48 KB of static memory)
+template <bool DEEP>
+__host__ __device__ constexpr int lv_ipt() {
+  return DEEP ? 4 : 8;
+}
 
 // Per body: first level it starts a cell at (common prefix with the previous
 // key + 1), its leaf level, whether it starts a group; per warp: how many
@@ -581,6 +585,7 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
                                                    const int32_t *__restrict__ offs, int S, int n_leaf, int n_crit,
                                                    uint8_t *lohi, uint8_t *gstart, uint32_t *rowcnt, int W) {
   const int DD = DEEP ? D : kLevels;
+  constexpr int kLvIpt = lv_ipt<DEEP>(), kLvTile = kBlock * kLvIpt;
   __shared__ uint64_t s_key[kLvTile + 2 * kHalo];
   __shared__ uint64_t s_klo[DEEP ? kLvTile + 2 * kHalo : 1];
   // common prefix (levels) of the keys at shared positions a and b
@@ -991,7 +996,7 @@ cudaError_t launch_sort(Ctx &c, cudaStream_t s) {
   if (e) return e;
   e = cudaMemsetAsync(c.sort_tile_ctr, 0, sizeof(uint32_t) * passes, s);
   if (e) return e;
-  int hb = min(cdiv(n, kBlock), c.num_sms * 4);
+  int hb = min(cdiv(n, kBlock), c.num_sms * 8);
   k_sort_hist<<<hb, kBlock, sizeof(uint32_t) * passes * 256, s>>>(deep ? c.key_lo0 : nullptr,
                                                                    deep ? c.key_hi0 : c.key[0], n, lo_passes, passes,
                                                                    c.offs, c.n_sys, c.sort_hist);
@@ -1082,8 +1087,8 @@ static cudaError_t cells_impl(Ctx &c, cudaStream_t s) {
   const int n = (int)c.n, D = c.levels;
   const int W = cdiv(n, 32);
   const int nb = cdiv(n, kBlock);
-  k_levels<FOREST, DEEP><<<cdiv(n, kLvTile), kBlock, 0, s>>>(c.key[0], c.skey_lo, D, n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit,
-                                               c.lohi, c.gstart, c.rowcnt, W);
+  k_levels<FOREST, DEEP><<<cdiv(n, kBlock * lv_ipt<DEEP>()), kBlock, 0, s>>>(
+      c.key[0], c.skey_lo, D, n, c.offs, c.n_sys, c.p.n_leaf, c.p.n_crit, c.lohi, c.gstart, c.rowcnt, W);
   c.launches++;
   cudaError_t e = launch_scan_u32(c, c.rowcnt, c.rowoff, (int64_t)(D + 2) * W, s);
   if (e) return e;
