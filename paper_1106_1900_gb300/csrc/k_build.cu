@@ -575,6 +575,20 @@ __host__ __device__ constexpr int lv_ipt() {
   return DEEP ? 4 : 8;
 }
 
+// Transpose of the warp's 32 x 32 bit matrix whose row r is lane r's word:
+// returns column `lane` (bit r = bit `lane` of lane r's word).  Five rounds
+// swap the off-diagonal blocks of halves, quarters, ... with xor shuffles.
+__device__ __forceinline__ unsigned warp_transpose32(unsigned x, int lane) {
+  const unsigned m[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+  int j = 16;
+#pragma unroll
+  for (int i = 0; i < 5; ++i, j >>= 1) {
+    const unsigned y = __shfl_xor_sync(kFull, x, j);
+    x = (lane & j) ? ((x & ~m[i]) | ((y >> j) & m[i])) : ((x & m[i]) | ((y << j) & ~m[i]));
+  }
+  return x;
+}
+
 // Per body: first level it starts a cell at (common prefix with the previous
 // key + 1), its leaf level, whether it starts a group; per warp: how many
 // cells it starts at each level and how many groups.  DEEP: keys of D > 20
@@ -682,13 +696,11 @@ __global__ void __launch_bounds__(kBlock) k_levels(const uint64_t *__restrict__ 
     }
     const int lane = threadIdx.x & 31;
     const int w = i >> 5;
-    uint32_t mine = 0;
-#pragma unroll
-    for (int k = 0; k <= (DEEP ? kLevelsMax : kLevels); ++k) {
-      if (DEEP && k > DD) break;
-      unsigned b = __ballot_sync(kFull, ok && lo <= k && k <= hi);
-      if (lane == k) mine = __popc(b);
-    }
+    // the levels this body starts a cell at, bits lo..hi (hi <= 30); the
+    // warp's 32 such words transposed give lane k the bodies starting a cell
+    // at level k
+    const unsigned levels = (ok && lo <= hi) ? ((2u << hi) - (1u << lo)) : 0u;
+    uint32_t mine = (uint32_t)__popc(warp_transpose32(levels, lane));
     unsigned bg = __ballot_sync(kFull, ok && gs);
     if (lane == DD + 1) mine = __popc(bg);  // rows 0..D: cells per level; row D + 1: groups
     if (lane < DD + 2 && w < W) rowcnt[(size_t)lane * W + w] = mine;
@@ -722,10 +734,15 @@ __global__ void __launch_bounds__(kBlock) k_emit(int n, int D, const int32_t *__
   // rows), lane r holding row r, all loaded at once
   const int lane = threadIdx.x & 31;
   const uint32_t myoff = (lane <= DD + 1 && w < W) ? rowoff[(size_t)lane * W + w] : 0u;
+  // the levels at which some lane of this warp starts a cell
+  const bool starts = ok && lo <= hi;
+  const int kmin = __reduce_min_sync(kFull, starts ? lo : DD + 1);
+  const int kmax = __reduce_max_sync(kFull, starts ? hi : -1);
   int prev = -1;
-  unsigned pb = 0;      // which lanes started a cell one level up
-  uint32_t poff = 0;    // this warp's offset one level up
-  for (int k = 0; k <= DD; ++k) {
+  unsigned pb = 0;  // which lanes started a cell one level up (none below kmin)
+  // this warp's offset one level up
+  uint32_t poff = (kmin >= 1 && kmin <= DD) ? __shfl_sync(kFull, myoff, kmin - 1) : 0u;
+  for (int k = kmin; k <= kmax; ++k) {
     bool in = ok && lo <= k && k <= hi;
     unsigned b = __ballot_sync(kFull, in);
     const uint32_t off = __shfl_sync(kFull, myoff, k);
